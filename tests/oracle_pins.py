@@ -1,0 +1,343 @@
+"""Pins for the FP64 oracle: checks against what the paper and the mathematics
+fix, independent of the oracle's own code paths.
+
+Each ``pin_*`` takes the loaded oracle library (so the mutation test can run
+them against deliberately broken builds) and raises AssertionError on failure.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+import oracle
+import synth
+
+C0 = synth.C0
+
+
+def _radar(**kw):
+    base = dict(n_samples=64, n_rx=2, os=4)
+    base.update(kw)
+    return synth.Radar(**base)
+
+
+def _point_scene(radar, M, target, amp, offset=(0.0, 0.0)):
+    q_tx, q_rx = synth.trajectory(radar, M, offset=offset)
+    tgt = np.asarray(target, dtype=np.float64)[None, :] + np.asarray(offset)[None, :]
+    beat = synth.beat_signal(radar, q_tx, q_rx, tgt, np.array([amp]))
+    return q_tx, q_rx, beat
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# --------------------------------------------------------------------------
+# transforms and windows
+# --------------------------------------------------------------------------
+def pin_fft(lib):
+    """Oracle FFT = numpy's (i)fft (library routine) = direct-sum DFT."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    for n in (1, 2, 8, 64, 1024):
+        x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        Xp = oracle.fft(x, +1, lib=lib)
+        Xm = oracle.fft(x, -1, lib=lib)
+        assert np.allclose(Xp, np.fft.ifft(x) * n, rtol=0, atol=1e-9 * max(1, n))
+        assert np.allclose(Xm, np.fft.fft(x), rtol=0, atol=1e-9 * max(1, n))
+    # textbook DFT with zero padding vs an explicit numpy matrix product
+    x = rng.standard_normal(12) + 1j * rng.standard_normal(12)
+    k = np.arange(48)[:, None]
+    n = np.arange(12)[None, :]
+    ref = np.exp(2j * np.pi * n * k / 48) @ x
+    assert np.allclose(oracle.dft(x, 48, +1, lib=lib), ref, atol=1e-10)
+
+
+def pin_windows(lib):
+    """Hann / Kaiser / rect against numpy's window routines."""
+    for L in (1, 2, 7, 64, 255):
+        assert np.allclose(oracle.window(oracle.WINDOW_HANN, L, lib=lib),
+                           np.hanning(L) if L > 1 else np.ones(1), atol=1e-15)
+        assert np.allclose(oracle.window(oracle.WINDOW_KAISER, L, 6.0, lib=lib),
+                           np.kaiser(L, 6.0), atol=1e-12)
+        assert np.all(oracle.window(oracle.WINDOW_RECT, L, lib=lib) == 1.0)
+
+
+def pin_range_compress(lib):
+    """Range compression = per-row textbook DFT of the windowed row."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    M, R, N, os_ = 3, 2, 16, 4
+    beat = rng.standard_normal((M, R, N)) + 1j * rng.standard_normal((M, R, N))
+    w = np.hanning(N)
+    S = oracle.range_compress(beat, w, os_, +1, lib=lib)
+    k = np.arange(N * os_)[:, None]
+    n = np.arange(N)[None, :]
+    E = np.exp(2j * np.pi * n * k / (N * os_))
+    ref = np.einsum("kn,mrn->mrk", E, beat * w)
+    assert np.allclose(S, ref, atol=1e-10)
+    Sm = oracle.range_compress(beat, w, os_, -1, lib=lib)
+    assert np.allclose(Sm, np.einsum("kn,mrn->mrk", E.conj(), beat * w), atol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# point-target closed forms
+# --------------------------------------------------------------------------
+def pin_matched_filter_closed_form(lib):
+    """Noiseless stop-and-hop point target on a pixel: every term of the
+    matched filter is a * sum(w_r) * w_az[m], so |P_bf| = |a| R sum(w_az) sum(w_r)
+    (rect windows: |a| R M N, the pulse-count-times-amplitude sum)."""
+    radar = _radar()
+    M = 24
+    a = 0.7 * np.exp(0.4j)
+    tgt = (0.3, 3.0)
+    q_tx, q_rx, beat = _point_scene(radar, M, tgt, a)
+    N, R = radar.n_samples, radar.n_rx
+    P = oracle.matched_filter(radar, beat, np.ones(N), q_tx, q_rx,
+                              np.array([tgt]), lib=lib)
+    assert abs(P[0] - a * R * M * N) < 1e-9 * abs(a) * R * M * N
+    w_az = np.hanning(M)
+    w_r = np.hanning(N)
+    P = oracle.matched_filter(radar, beat, w_r, q_tx, q_rx, np.array([tgt]), w_az=w_az,
+                              lib=lib)
+    ref = a * R * w_az.sum() * w_r.sum()
+    assert abs(P[0] - ref) < 1e-9 * abs(ref)
+    # conjugate convention: beat generated with the opposite sign convention
+    # images to the conjugate
+    Pm = oracle.matched_filter(radar, beat.conj(), np.ones(N), q_tx, q_rx,
+                               np.array([tgt]), sign=-1, lib=lib)
+    assert abs(Pm[0] - np.conj(a) * R * M * N) < 1e-9 * abs(a) * R * M * N
+
+
+def pin_backproject_point_target(lib):
+    """FFT + linear interpolation at the target: within the interpolation loss
+    of the closed form, phase equal to arg(a), peak on the true pixel."""
+    radar = _radar(os=4)
+    M = 24
+    a = 1.3 * np.exp(-1.1j)
+    tgt = (0.3, 3.0)
+    q_tx, q_rx, beat = _point_scene(radar, M, tgt, a)
+    N, R = radar.n_samples, radar.n_rx
+    S = oracle.range_compress(beat, np.ones(N), radar.os, lib=lib)
+    P = oracle.backproject(radar, S, q_tx, q_rx, np.array([tgt]), lib=lib)[0]
+    ref = a * R * M * N
+    ratio = abs(P) / abs(ref)
+    # linear interpolation between bins whose phases differ by ~pi/os loses at
+    # most 1 - cos(pi / (2 os)) at mid-bin, plus the Dirichlet roll-off
+    assert 0.85 <= ratio <= 1.0 + 1e-9, ratio
+    assert abs(np.angle(P / ref)) < 0.05
+    # peak on the true pixel of a local grid at a third of the range
+    # resolution (finer grids resolve the interpolation ripple instead)
+    g = synth.Grid(x0=tgt[0] - 0.2, y0=tgt[1] - 0.2, dx=0.05, dy=0.05, nx=9, ny=9)
+    img = oracle.backproject(radar, S, q_tx, q_rx, g.pixels(), lib=lib)
+    assert int(np.argmax(np.abs(img))) == 4 * 9 + 4
+
+
+def pin_interpolation_convergence(lib):
+    """FFT + lerp converges to the brute-force matched filter as the
+    zero-padding factor grows: linear interpolation is second order, so the
+    error falls by ~4 per doubling of os."""
+    rng = np.random.Generator(np.random.PCG64(3))
+    M = 16
+    tg = np.stack([rng.uniform(-0.5, 0.5, 3), rng.uniform(2.5, 3.5, 3)], 1)
+    am = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+    g = synth.Grid(x0=-0.6, y0=2.4, dx=0.1, dy=0.1, nx=13, ny=13)
+    errs = []
+    for os_ in (4, 8, 16):
+        radar = _radar(os=os_)
+        q_tx, q_rx = synth.trajectory(radar, M)
+        beat = synth.beat_signal(radar, q_tx, q_rx, tg, am)
+        w_r = np.hanning(radar.n_samples)
+        ref = oracle.matched_filter(radar, beat, w_r, q_tx, q_rx, g.pixels(), lib=lib)
+        S = oracle.range_compress(beat, w_r, os_, lib=lib)
+        img = oracle.backproject(radar, S, q_tx, q_rx, g.pixels(), lib=lib)
+        errs.append(rel_l2(img, ref))
+    assert errs[0] < 0.1, errs
+    assert errs[1] / errs[0] < 0.35 and errs[2] / errs[1] < 0.35, errs
+
+
+def _minus3db_width(coord, mag):
+    """Full width at half power of a sampled main lobe (linear edges)."""
+    p = mag / mag.max()
+    k = int(np.argmax(p))
+    thr = 1 / math.sqrt(2)
+    i = k
+    while p[i] > thr:
+        i -= 1
+    left = coord[i] + (thr - p[i]) / (p[i + 1] - p[i]) * (coord[i + 1] - coord[i])
+    j = k
+    while p[j] > thr:
+        j += 1
+    right = coord[j - 1] + (p[j - 1] - thr) / (p[j - 1] - p[j]) * (coord[j] - coord[j - 1])
+    return right - left
+
+
+def pin_resolution(lib):
+    """-3 dB widths of a point target: range 0.886 c / 2B with rect and
+    1.44 c / 2B with Hann range windows (textbook DFT main lobes); azimuth
+    0.886 lambda y / 2L for a rect aperture of length L."""
+    radar = _radar(n_samples=128, n_rx=1, os=4)
+    M = 256
+    tgt = (0.0, 4.0)
+    q_tx, q_rx, beat = _point_scene(radar, M, tgt, 1.0)
+    N = radar.n_samples
+    ys = np.arange(-0.3, 0.3, 0.002) + tgt[1]
+    line = np.stack([np.zeros_like(ys), ys], 1)
+    res = C0 / (2 * radar.bandwidth)
+    for w_r, k_w in ((np.ones(N), 0.886), (np.hanning(N), 1.44)):
+        P = oracle.matched_filter(radar, beat, w_r, q_tx, q_rx, line, lib=lib)
+        width = _minus3db_width(ys, np.abs(P))
+        assert abs(width / (k_w * res) - 1) < 0.10, (width, k_w * res)
+    xs = np.arange(-0.08, 0.08, 0.0005)
+    line = np.stack([xs, np.full_like(xs, tgt[1])], 1)
+    P = oracle.matched_filter(radar, beat, np.ones(N), q_tx, q_rx, line, lib=lib)
+    L = (M - 1) * 10.0 * radar.pri
+    az = 0.886 * radar.wavelength * tgt[1] / (2 * L)
+    width = _minus3db_width(xs, np.abs(P))
+    assert abs(width / az - 1) < 0.10, (width, az)
+
+
+# --------------------------------------------------------------------------
+# invariants of the backprojection
+# --------------------------------------------------------------------------
+def _small_case(lib, R=2, M=20, seed=1, offset=(0.0, 0.0)):
+    radar = _radar(n_rx=R)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    q_tx, q_rx = synth.trajectory(radar, M, jitter=0.01, rng=rng, offset=offset)
+    tg = np.stack([rng.uniform(-0.8, 0.8, 4), rng.uniform(2.0, 4.0, 4)], 1)
+    tg = tg + np.asarray(offset)
+    am = rng.standard_normal(4) + 1j * rng.standard_normal(4)
+    g = synth.Grid(x0=-1.0 + offset[0], y0=1.8 + offset[1], dx=0.07, dy=0.07,
+                   nx=30, ny=33)
+    return radar, q_tx, q_rx, tg, am, g
+
+
+def pin_linearity(lib):
+    """P(s1 + s2) = P(s1) + P(s2) (range compression and BP are linear)."""
+    radar, q_tx, q_rx, tg, am, g = _small_case(lib)
+    b1 = synth.beat_signal(radar, q_tx, q_rx, tg[:2], am[:2])
+    b2 = synth.beat_signal(radar, q_tx, q_rx, tg[2:], am[2:])
+    w = np.hanning(radar.n_samples)
+    wa = np.hanning(len(q_tx))
+
+    def img(b):
+        S = oracle.range_compress(b, w, radar.os, lib=lib)
+        return oracle.backproject(radar, S, q_tx, q_rx, g.pixels(), w_az=wa, lib=lib)
+
+    assert rel_l2(img(b1) + img(b2), img(b1 + b2)) < 1e-12
+
+
+def pin_alg1_equals_alg2(lib):
+    """Alg. 1 without velocity (vector window) and Alg. 2 without Doppler give
+    the same image: the paper's mathematical optimisation changes nothing
+    (Table II row 3, Delta SNR 0)."""
+    radar, q_tx, q_rx, tg, am, g = _small_case(lib)
+    b = synth.beat_signal(radar, q_tx, q_rx, tg, am)
+    S = oracle.range_compress(b, np.hanning(radar.n_samples), radar.os, lib=lib)
+    wa = np.hanning(len(q_tx))
+    i1 = oracle.backproject_alg1(radar, S, q_tx, q_rx, g.pixels(), w_az=wa, lib=lib)
+    i2 = oracle.backproject(radar, S, q_tx, q_rx, g.pixels(), w_az=wa, lib=lib)
+    assert rel_l2(i1, i2) < 1e-10
+
+
+def pin_rx_halving(lib):
+    """Halving the Rx count halves a calibrated point target's peak
+    (-6.02 dB, Sec. III-F)."""
+    radar = _radar(n_rx=4)
+    M = 24
+    tgt = (0.2, 3.3)
+    q_tx, q_rx, beat = _point_scene(radar, M, tgt, 1.0)
+    N = radar.n_samples
+    p4 = oracle.matched_filter(radar, beat, np.ones(N), q_tx, q_rx, np.array([tgt]),
+                               lib=lib)[0]
+    p2 = oracle.matched_filter(radar, beat[:, :2], np.ones(N), q_tx, q_rx[:, :2],
+                               np.array([tgt]), lib=lib)[0]
+    assert abs(abs(p2) / abs(p4) - 0.5) < 1e-9
+    S = oracle.range_compress(beat, np.ones(N), radar.os, lib=lib)
+    b4 = oracle.backproject(radar, S, q_tx, q_rx, np.array([tgt]), lib=lib)[0]
+    b2 = oracle.backproject(radar, S[:, :2], q_tx, q_rx[:, :2], np.array([tgt]),
+                            lib=lib)[0]
+    assert abs(abs(b2) / abs(b4) - 0.5) < 0.02
+
+
+def pin_single_term(lib):
+    """One pixel, one chirp, one Rx, hand-computed.
+
+    c = 4, f0 = 1/6, slope / fs = 0.4375, N_fft = 16:
+      a1 = slope N_fft / (c fs) = 0.4375 * 16 / 4 = 1.75 bins per metre.
+    Tx and Rx at the origin, pixel at (0, 3): d_hyp = 6 m, f_ind = 10.5,
+    i0 = 10, f = 0.5, v = (S[10] + S[11]) / 2 = ((2+1j) + (4-1j)) / 2 = 3;
+    s_hyp = exp(j 2 pi f0 d / c) = exp(j pi / 2) = j;  w_sar = 0.5
+      => P = 1.5 j  (conjugate convention: -1.5 j).
+    Base bin outside the crop range contributes nothing.
+    """
+    radar = synth.Radar(f0=1.0 / 6.0, bandwidth=0.4375 * 8.0, t_chirp=1.0,
+                        n_samples=8, n_rx=1, os=2, c=4.0)
+    assert abs(radar.slope / radar.fs - 0.4375) < 1e-15
+    S = np.zeros((1, 1, 16), np.complex128)
+    S[0, 0, 10] = 2 + 1j
+    S[0, 0, 11] = 4 - 1j
+    q = np.zeros((1, 2))
+    qr = np.zeros((1, 1, 2))
+    px = np.array([[0.0, 3.0]])
+    P = oracle.backproject(radar, S, q, qr, px, w_az=np.array([0.5]), lib=lib)[0]
+    assert abs(P - 1.5j) < 1e-12, P
+    Pm = oracle.backproject(radar, S, q, qr, px, w_az=np.array([0.5]), sign=-1,
+                            lib=lib)[0]
+    assert abs(Pm + 1.5j) < 1e-12, Pm
+    P1 = oracle.backproject_alg1(radar, S, q, qr, px, w_az=np.array([0.5]), lib=lib)[0]
+    assert abs(P1 - 1.5j) < 1e-12, P1
+    for crop in ((0, 10), (11, 15)):
+        Pc = oracle.backproject(radar, S, q, qr, px, crop=crop, lib=lib)[0]
+        assert Pc == 0, (crop, Pc)
+    Pc = oracle.backproject(radar, S, q, qr, px, crop=(10, 11), lib=lib)[0]
+    assert abs(Pc - 3j) < 1e-12
+
+
+def pin_subaperture_additivity(lib):
+    """BP over [0, M) = BP over [0, k) + BP over [k, M)."""
+    radar, q_tx, q_rx, tg, am, g = _small_case(lib, M=21)
+    b = synth.beat_signal(radar, q_tx, q_rx, tg, am)
+    S = oracle.range_compress(b, np.hanning(radar.n_samples), radar.os, lib=lib)
+    wa = np.hanning(len(q_tx))
+    full = oracle.backproject(radar, S, q_tx, q_rx, g.pixels(), w_az=wa, lib=lib)
+    k = 8
+    a = oracle.backproject(radar, S[:k], q_tx[:k], q_rx[:k], g.pixels(), w_az=wa[:k],
+                           lib=lib)
+    b_ = oracle.backproject(radar, S[k:], q_tx[k:], q_rx[k:], g.pixels(), w_az=wa[k:],
+                            lib=lib)
+    assert rel_l2(a + b_, full) < 1e-12
+
+
+def pin_translation_invariance(lib):
+    """Moving scene and trajectory by (1000 m, 1000 m) leaves the image
+    unchanged (FP64 positions keep the 77 GHz phase)."""
+    imgs = []
+    for off in ((0.0, 0.0), (1000.0, 1000.0)):
+        radar, q_tx, q_rx, tg, am, g = _small_case(lib, offset=off)
+        b = synth.beat_signal(radar, q_tx, q_rx, tg, am)
+        S = oracle.range_compress(b, np.hanning(radar.n_samples), radar.os, lib=lib)
+        imgs.append(oracle.backproject(radar, S, q_tx, q_rx, g.pixels(), lib=lib))
+    assert rel_l2(imgs[1], imgs[0]) < 1e-6
+
+
+def pin_bp_matches_matched_filter(lib):
+    """On a multi-target scene the oracle image is within the os = 16
+    interpolation error of the brute-force matched filter."""
+    radar, q_tx, q_rx, tg, am, g = _small_case(lib)
+    radar = _radar(n_rx=2, os=16)
+    b = synth.beat_signal(radar, q_tx, q_rx, tg, am)
+    w = np.hanning(radar.n_samples)
+    wa = np.hanning(len(q_tx))
+    ref = oracle.matched_filter(radar, b, w, q_tx, q_rx, g.pixels(), w_az=wa, lib=lib)
+    S = oracle.range_compress(b, w, radar.os, lib=lib)
+    img = oracle.backproject(radar, S, q_tx, q_rx, g.pixels(), w_az=wa, lib=lib)
+    assert rel_l2(img, ref) < 5e-3
+
+
+ALL_PINS = [
+    pin_fft, pin_windows, pin_range_compress, pin_matched_filter_closed_form,
+    pin_backproject_point_target, pin_interpolation_convergence, pin_resolution,
+    pin_linearity, pin_alg1_equals_alg2, pin_rx_halving, pin_single_term,
+    pin_subaperture_additivity, pin_translation_invariance,
+    pin_bp_matches_matched_filter,
+]
