@@ -1,0 +1,225 @@
+/*
+ * sar.h -- C ABI of the GB300-native automotive FMCW SAR imaging library
+ * (range compression + time-domain backprojection, after "Implementation of
+ * Real-Time Automotive SAR Imaging", arXiv 2306.09784).
+ *
+ * General rules
+ *  - Every call returns an int status (enum sar_status); no C++ exception
+ *    crosses this boundary.
+ *  - Pointers named *_dev are CUDA device pointers on the plan's device;
+ *    pointers named *_host are host pointers (pinned memory gives the fastest
+ *    copies).  The caller owns every buffer it passes in; the plan owns only
+ *    its tables and scratch.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls that take a stream are asynchronous: they validate their
+ *    arguments on the host, enqueue kernels and return.  Errors raised inside
+ *    kernels are reported by sar_plan_check_errors() after the work finished.
+ *  - Units are SI (metres, seconds, hertz).  Geometry is 2-D (x, y): the
+ *    paper computes 2-D distances (Alg. 1, Sec. II).
+ *  - Complex values are interleaved (re, im) pairs: complex64 = 2 x float.
+ *  - Calls on one plan must not overlap in time from several host threads.
+ */
+#ifndef SAR_H
+#define SAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum sar_status {
+    SAR_OK = 0,
+    SAR_EINVAL = 1,    /* invalid argument (null pointer, size, parameter) */
+    SAR_ENOMEM = 2,    /* device allocation failed or HBM budget exceeded */
+    SAR_EAGAIN = 3,    /* not ready yet (poll) or admission queue full */
+    SAR_ETIMEOUT = 4,  /* a bounded wait ran out */
+    SAR_ECUDA = 5,     /* a CUDA runtime call failed */
+    SAR_EBOUNDS = 6,   /* a kernel saw invalid geometry (non-finite or out of range) */
+    SAR_ENOTFOUND = 7  /* unknown ticket */
+};
+
+enum sar_window { SAR_WINDOW_RECT = 0, SAR_WINDOW_HANN = 1, SAR_WINDOW_KAISER = 2 };
+
+/* Storage of the range profiles between the two stages. */
+enum sar_precision {
+    SAR_PREC_FP32 = 0,  /* complex64 samples */
+    SAR_PREC_FP16 = 1   /* half-precision complex samples with one FP32 scale per (chirp, Rx) */
+};
+
+/*
+ * Radar and processing parameters (paper Table I, Sec. II, Sec. III-C).
+ *  f0          frequency at the range transform's time origin (sample 0), Hz
+ *  slope       chirp slope mu = B / T_P, Hz/s
+ *  fs          beat-signal sample rate, Hz
+ *  c           propagation speed, m/s
+ *  n_samples   N, samples per chirp and Rx
+ *  os          zero-padding factor; N_fft = N * os must be a power of two
+ *              between 64 and 16384
+ *  n_rx        R, Rx channels per chirp (1..64)
+ *  max_pulses  capacity in chirps per call (sizes the plan's scratch)
+ *  range_window    enum sar_window applied to each chirp before the transform
+ *  kaiser_beta     beta of the Kaiser window
+ *  precision   enum sar_precision of the range profiles
+ *  phase_sign  +1: range transform kernel exp(+j 2 pi n k / N_fft) and phase
+ *              correction exp(+j 2 pi f0 d / c) (beat taken as Rx conj(Tx));
+ *              -1: the conjugate convention (forward transform, exp(-j ...))
+ *  crop_lo, crop_hi  interpolation base bins kept, [crop_lo, crop_hi);
+ *              terms whose base bin falls outside contribute nothing.
+ *              0, 0 selects the full valid range [0, N_fft - 1).
+ *  max_doppler_bins  bound on |f_doppler(p)| (in bins) of the Doppler
+ *              offsets passed to sar_backproject; the staged bin windows are
+ *              widened by it.  Offsets beyond the bound are clamped to it.
+ */
+typedef struct sar_radar_params {
+    double f0;
+    double slope;
+    double fs;
+    double c;
+    int32_t n_samples;
+    int32_t os;
+    int32_t n_rx;
+    int32_t max_pulses;
+    int32_t range_window;
+    int32_t precision;
+    double kaiser_beta;
+    int32_t phase_sign;
+    int32_t crop_lo;
+    int32_t crop_hi;
+    int32_t reserved;
+    double max_doppler_bins;
+} sar_radar_params;
+
+/*
+ * Reconstruction points (paper Sec. III-E: Cartesian reference grid or any
+ * other set of points, e.g. a polar grid).
+ *  pixels_xy == NULL: Cartesian grid, pixel (ix, iy) at
+ *      (x0 + ix dx, y0 + iy dy), image stored [ny][nx] with x fastest;
+ *  pixels_xy != NULL: host array [n_pixels][2] of (x, y) points, image
+ *      stored [n_pixels] in the caller's order; x0..ny are ignored.
+ * The plan copies what it needs; the caller may free pixels_xy afterwards.
+ */
+typedef struct sar_grid {
+    double x0, y0, dx, dy;
+    int32_t nx, ny;
+    const double *pixels_xy;
+    int64_t n_pixels;
+} sar_grid;
+
+typedef struct sar_plan sar_plan;
+
+/* Sizes derived by a plan (all read-only). */
+typedef struct sar_plan_info {
+    int32_t n_fft;              /* N * os */
+    int32_t n_bins;             /* samples per stored range profile = crop_hi - crop_lo + 1 */
+    int32_t crop_lo, crop_hi;
+    int64_t n_pixels;           /* image size in complex64 values */
+    int32_t n_tiles;            /* pixel tiles of 1024 reconstruction points */
+    int32_t window_bins;        /* bins staged per (tile, chirp, Rx) */
+    int32_t pulses_per_block;   /* chirps staged per pipeline step */
+    int32_t bp_ctas;            /* persistent backprojection grid size */
+    double bins_per_metre;      /* a1 = mu N_fft / (c fs) */
+    double cycles_per_bin;      /* f0 / (c a1) */
+    size_t device_bytes;        /* device memory the plan owns */
+} sar_plan_info;
+
+/*
+ * Create a plan on the current CUDA device.  Validates the parameters,
+ * builds the FP64 tables (range window, transform twiddles, per-bin phase
+ * rotation, pixel tiles) and allocates the plan's device memory.
+ * hbm_budget_bytes bounds that memory (0 = no bound): SAR_ENOMEM if it
+ * would be exceeded.  *out receives the plan (NULL on error).
+ */
+int sar_plan_create(const sar_radar_params *params, const sar_grid *grid,
+                    size_t hbm_budget_bytes, sar_plan **out);
+
+/* Release a plan and its device memory (synchronises its device). NULL is a no-op. */
+void sar_plan_destroy(sar_plan *plan);
+
+int sar_plan_get_info(const sar_plan *plan, sar_plan_info *info);
+
+/* Bytes of the range-profile buffer that sar_range_compress fills for M chirps. */
+int sar_profile_bytes(const sar_plan *plan, int32_t M, size_t *bytes);
+
+/*
+ * Range compression (paper: the beat spectrum s(f, m, n_rx) that Alg. 1
+ * and Alg. 2 interpolate at f_hyp / f_ind; its equidistant beat-frequency
+ * axis, Sec. III-C).  For every chirp m < M and Rx r:
+ *     S[m][r][k] = sum_{n<N} w_r[n] beat[m][r][n] exp(sign j 2 pi n k / N_fft)
+ * and the stored profile, for bins k = crop_lo .. crop_hi, is
+ *     prof[m][r][k - crop_lo] = w_sar[m] exp(sign j 2 pi frac(k f0 / (c a1))) S[m][r][k]
+ * i.e. the spectrum with the window w_sar (Sec. III-B, NULL = ones) and the
+ * per-bin part of the phase correction exp(sign j 2 pi f0 d / c) folded in
+ * (d = index / a1 on the bin axis, so the correction splits into a per-bin
+ * factor and a factor of the fractional index).
+ *  beat_dev   complex64 [M][R][N]
+ *  w_az_dev   float [M] or NULL
+ *  prof_dev   sar_profile_bytes(M) bytes, 256-byte aligned.  Layout:
+ *             FP32: complex64 [M][R][n_bins];
+ *             FP16: float scale[M][R], padded to a 256-byte multiple, then
+ *                   half2 [M][R][n_bins] with value = scale * half.
+ * Errors: SAR_EINVAL (null pointers, M < 1 or M > max_pulses, misalignment).
+ */
+int sar_range_compress(sar_plan *plan, const void *beat_dev, int32_t M,
+                       const float *w_az_dev, void *prof_dev, void *stream);
+
+/*
+ * The plain windowed, zero-padded range transform S[m][r][k] for all
+ * k < N_fft as complex64 [M][R][N_fft] (same kernel as sar_range_compress,
+ * without window w_sar, rotation or crop).  For inspection and parity checks.
+ */
+int sar_range_spectrum(sar_plan *plan, const void *beat_dev, int32_t M,
+                       void *spec_dev, void *stream);
+
+/*
+ * Backprojection, paper Alg. 2 (Sec. IV): for every reconstruction point p
+ *     P(p) = sum_{m<M} sum_{r<R} exp(sign j 2 pi f0 d / c) s(a1 d + f_doppler(p), m, r)
+ * with d = ||p - q_tx(m)|| + ||p - q_rx(m, r)|| and s(., m, r) the linear
+ * interpolation of the stored profile (w_sar already folded in).
+ *  prof_dev        output of sar_range_compress for these M chirps
+ *  q_tx_dev        double [M][2] Tx positions
+ *  q_rx_dev        double [M][R][2] Rx positions
+ *  fdopp_idx_dev   float [n_pixels] Doppler index offsets f_doppler(p) in bins
+ *                  (f_doppler of Alg. 2), or NULL for none
+ *  image_dev       complex64 [n_pixels]; written (accumulate = 0) or added to
+ *                  (accumulate = 1, for sub-aperture accumulation)
+ * Errors: SAR_EINVAL; non-finite or absurd geometry (beyond 1e6 m) is
+ * skipped and flagged for sar_plan_check_errors (SAR_EBOUNDS).
+ */
+int sar_backproject(sar_plan *plan, const void *prof_dev, int32_t M,
+                    const double *q_tx_dev, const double *q_rx_dev,
+                    const float *fdopp_idx_dev, void *image_dev,
+                    int32_t accumulate, void *stream);
+
+/*
+ * Whole frame from host memory: copy beat, w_sar and trajectory to the
+ * plan's device staging buffers, range-compress, backproject and copy the
+ * image back to image_host, all on `stream`; returns after the image is in
+ * host memory (the call synchronises the stream).  Staging buffers are
+ * allocated on first use for max_pulses chirps (counted in the HBM budget).
+ *  beat_host  complex64 [M][R][N];  w_az_host float [M] or NULL;
+ *  q_tx_host  double [M][2];  q_rx_host double [M][R][2];
+ *  image_host complex64 [n_pixels].
+ */
+int sar_form_image_host(sar_plan *plan, const void *beat_host, int32_t M,
+                        const float *w_az_host, const double *q_tx_host,
+                        const double *q_rx_host, void *image_host, void *stream);
+
+/*
+ * Waits for the plan's device work and reports (then clears) kernel-side
+ * error flags: SAR_OK or SAR_EBOUNDS.
+ */
+int sar_plan_check_errors(sar_plan *plan);
+
+/* Static text for a status code. */
+const char *sar_status_string(int status);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int sar_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAR_H */

@@ -7,7 +7,7 @@
  * reference legs may load or call it.  The CUDA library never does, and this
  * file shares no code, header, table or constant with it.
  *
- * Conventions (all readings of the paper are listed in the design doc):
+ * Conventions (readings where the paper is silent or garbled):
  *  - complex arrays are interleaved (re, im) doubles;
  *  - 2-D geometry (Sec. II: "2D distance"); positions are (x, y) pairs;
  *  - `sign` = +1 selects the +j range-transform kernel and the phase
@@ -16,8 +16,8 @@
  *    lies outside [crop_lo, crop_hi) contributes nothing (the default range
  *    is [0, N_fft - 1), i.e. both interpolation samples must exist).
  *
- * Parity status per function is stated in the design doc; every function below is
- * pinned by the -m "not gpu" tests (closed forms, brute force, invariants).
+ * Every function below is pinned by the -m "not gpu" tests (closed forms,
+ * brute force, invariants, planted mutations).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -240,7 +240,8 @@ API int oracle_backproject(double f0, double slope, double fs, double c, int n_f
  *   v_tx = <p - q_tx, v(m)> / d_tx,  v_rx = <p - q_rx, v(m)> / d_rx
  *   tau  = (d_tx + d_rx) / c
  *   f_hyp = mu tau + f0 (v_tx + v_rx) / c
- *   s_hyp = exp(sign j 2 pi f0 tau)       (f0 restored)
+ *   s_hyp = exp(sign j 2 pi f0 tau)       (the printed s_hyp lacks f0;
+ *                                           the phase of a delay tau is 2 pi f0 tau)
  *   P(p) += s_hyp * s(f_hyp) * w_sar(m)
  * The spectrum is sampled on the beat-frequency axis f_k = k fs / N_fft, so
  * s(f_hyp) is the linear interpolation at bin f_hyp N_fft / fs.

@@ -1,0 +1,257 @@
+"""GB300-native automotive FMCW SAR imaging: range compression and
+time-domain backprojection (after arXiv 2306.09784, Alg. 2).
+
+This module is a thin ctypes binding over the C ABI in include/sar.h
+(paper_2306_09784_gb300/_lib/libsar.so): argument marshalling only, every
+step of the imaging path runs in the library's CUDA kernels.  PyTorch tensors
+provide device memory and streams.  Importing fails loudly when the library
+has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsar.so")
+
+SAR_OK, SAR_EINVAL, SAR_ENOMEM, SAR_EAGAIN, SAR_ETIMEOUT, SAR_ECUDA, SAR_EBOUNDS, SAR_ENOTFOUND = range(8)
+WINDOW_RECT, WINDOW_HANN, WINDOW_KAISER = 0, 1, 2
+PREC_FP32, PREC_FP16 = 0, 1
+
+# Every symbol include/sar.h declares (checked by the tests).
+EXPORTS = (
+    "sar_plan_create", "sar_plan_destroy", "sar_plan_get_info", "sar_profile_bytes",
+    "sar_range_compress", "sar_range_spectrum", "sar_backproject", "sar_form_image_host",
+    "sar_plan_check_errors", "sar_status_string", "sar_version",
+)
+
+
+class SarError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+class RadarParams(ctypes.Structure):
+    _fields_ = [
+        ("f0", ctypes.c_double), ("slope", ctypes.c_double), ("fs", ctypes.c_double),
+        ("c", ctypes.c_double), ("n_samples", ctypes.c_int32), ("os", ctypes.c_int32),
+        ("n_rx", ctypes.c_int32), ("max_pulses", ctypes.c_int32),
+        ("range_window", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("kaiser_beta", ctypes.c_double), ("phase_sign", ctypes.c_int32),
+        ("crop_lo", ctypes.c_int32), ("crop_hi", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("max_doppler_bins", ctypes.c_double),
+    ]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [
+        ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("dx", ctypes.c_double),
+        ("dy", ctypes.c_double), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("pixels_xy", ctypes.c_void_p), ("n_pixels", ctypes.c_int64),
+    ]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_fft", ctypes.c_int32), ("n_bins", ctypes.c_int32), ("crop_lo", ctypes.c_int32),
+        ("crop_hi", ctypes.c_int32), ("n_pixels", ctypes.c_int64), ("n_tiles", ctypes.c_int32),
+        ("window_bins", ctypes.c_int32), ("pulses_per_block", ctypes.c_int32),
+        ("bp_ctas", ctypes.c_int32), ("bins_per_metre", ctypes.c_double),
+        ("cycles_per_bin", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libsar (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libsar not built ({path} missing): run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    vp, i32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+    lib.sar_plan_create.argtypes = [ctypes.POINTER(RadarParams), ctypes.POINTER(Grid), sz,
+                                    ctypes.POINTER(vp)]
+    lib.sar_plan_destroy.argtypes = [vp]
+    lib.sar_plan_destroy.restype = None
+    lib.sar_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+    lib.sar_profile_bytes.argtypes = [vp, i32, ctypes.POINTER(sz)]
+    lib.sar_range_compress.argtypes = [vp, vp, i32, vp, vp, vp]
+    lib.sar_range_spectrum.argtypes = [vp, vp, i32, vp, vp]
+    lib.sar_backproject.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32, vp]
+    lib.sar_form_image_host.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
+    lib.sar_plan_check_errors.argtypes = [vp]
+    lib.sar_status_string.argtypes = [ctypes.c_int]
+    lib.sar_status_string.restype = ctypes.c_char_p
+    lib.sar_version.argtypes = []
+    for name in EXPORTS:
+        fn = getattr(lib, name)
+        if name not in ("sar_plan_destroy", "sar_status_string"):
+            fn.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load_library().sar_status_string(status).decode()
+    except ImportError:
+        return f"status {status}"
+
+
+def _check(rc: int, what: str):
+    if rc != SAR_OK:
+        raise SarError(rc, what)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> Optional[int]:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _require_cuda(t, name, dtype=None):
+    import torch
+    if t is None:
+        return
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+
+
+class Plan:
+    """A sar_plan: radar parameters + reconstruction points on one device."""
+
+    def __init__(self, *, f0: float, slope: float, fs: float, c: float, n_samples: int,
+                 os_factor: int, n_rx: int, max_pulses: int, grid=None, pixels_xy=None,
+                 range_window: int = WINDOW_HANN, precision: int = PREC_FP32,
+                 kaiser_beta: float = 6.0, phase_sign: int = 1, crop=(0, 0),
+                 max_doppler_bins: float = 0.0, hbm_budget: int = 0):
+        self._lib = load_library()
+        self._plan = None
+        p = RadarParams(f0=f0, slope=slope, fs=fs, c=c, n_samples=n_samples, os=os_factor,
+                        n_rx=n_rx, max_pulses=max_pulses, range_window=range_window,
+                        precision=precision, kaiser_beta=kaiser_beta, phase_sign=phase_sign,
+                        crop_lo=int(crop[0]), crop_hi=int(crop[1]), reserved=0,
+                        max_doppler_bins=max_doppler_bins)
+        g = Grid()
+        self._pix_keep = None
+        if pixels_xy is not None:
+            import numpy as np
+            arr = np.ascontiguousarray(pixels_xy, dtype=np.float64).reshape(-1, 2)
+            self._pix_keep = arr
+            g.pixels_xy = arr.ctypes.data
+            g.n_pixels = len(arr)
+        else:
+            g.x0, g.y0, g.dx, g.dy, g.nx, g.ny = (grid.x0, grid.y0, grid.dx, grid.dy,
+                                                  grid.nx, grid.ny)
+        handle = ctypes.c_void_p()
+        _check(self._lib.sar_plan_create(ctypes.byref(p), ctypes.byref(g), hbm_budget,
+                                         ctypes.byref(handle)), "sar_plan_create")
+        self._plan = handle
+        self._pix_keep = None
+        self.params = p
+        self.info = PlanInfo()
+        _check(self._lib.sar_plan_get_info(self._plan, ctypes.byref(self.info)),
+               "sar_plan_get_info")
+
+    @classmethod
+    def from_radar(cls, radar, max_pulses: int, grid=None, pixels_xy=None, **kw):
+        """Build from a synth.Radar-like object (f0, slope, fs, c, n_samples, os, n_rx)."""
+        return cls(f0=radar.f0, slope=radar.slope, fs=radar.fs, c=radar.c,
+                   n_samples=radar.n_samples, os_factor=radar.os, n_rx=radar.n_rx,
+                   max_pulses=max_pulses, grid=grid, pixels_xy=pixels_xy, **kw)
+
+    def close(self):
+        if self._plan is not None:
+            self._lib.sar_plan_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._plan
+
+    @property
+    def n_pixels(self) -> int:
+        return int(self.info.n_pixels)
+
+    def profile_bytes(self, M: int) -> int:
+        n = ctypes.c_size_t()
+        _check(self._lib.sar_profile_bytes(self._plan, M, ctypes.byref(n)), "sar_profile_bytes")
+        return int(n.value)
+
+    def empty_profiles(self, M: int, device="cuda"):
+        import torch
+        return torch.empty(self.profile_bytes(M), dtype=torch.uint8, device=device)
+
+    def range_compress(self, beat, w_az=None, out=None, stream=None):
+        """beat: complex64 [M, R, N] CUDA tensor -> profile buffer (uint8)."""
+        import torch
+        _require_cuda(beat, "beat", torch.complex64)
+        _require_cuda(w_az, "w_az", torch.float32)
+        M = beat.shape[0]
+        if out is None:
+            out = self.empty_profiles(M, beat.device)
+        _check(self._lib.sar_range_compress(self._plan, _ptr(beat), M, _ptr(w_az), _ptr(out),
+                                            _stream(stream)), "sar_range_compress")
+        return out
+
+    def range_spectrum(self, beat, out=None, stream=None):
+        """beat: complex64 [M, R, N] -> complex64 [M, R, N_fft]."""
+        import torch
+        _require_cuda(beat, "beat", torch.complex64)
+        M, R, _ = beat.shape
+        if out is None:
+            out = torch.empty((M, R, int(self.info.n_fft)), dtype=torch.complex64,
+                              device=beat.device)
+        _check(self._lib.sar_range_spectrum(self._plan, _ptr(beat), M, _ptr(out),
+                                            _stream(stream)), "sar_range_spectrum")
+        return out
+
+    def backproject(self, prof, M: int, q_tx, q_rx, image=None, accumulate: bool = False,
+                    fdopp=None, stream=None):
+        """Alg. 2 into image (complex64 [n_pixels]); q_tx float64 [M, 2], q_rx [M, R, 2]."""
+        import torch
+        _require_cuda(q_tx, "q_tx", torch.float64)
+        _require_cuda(q_rx, "q_rx", torch.float64)
+        _require_cuda(fdopp, "fdopp", torch.float32)
+        if image is None:
+            image = torch.zeros(self.n_pixels, dtype=torch.complex64, device=q_tx.device)
+        _require_cuda(image, "image", torch.complex64)
+        _check(self._lib.sar_backproject(self._plan, _ptr(prof), M, _ptr(q_tx), _ptr(q_rx),
+                                         _ptr(fdopp), _ptr(image), 1 if accumulate else 0,
+                                         _stream(stream)), "sar_backproject")
+        return image
+
+    def form_image_host(self, beat, q_tx, q_rx, image, w_az=None, stream=None):
+        """Whole frame from host tensors (pinned for speed); blocks until done."""
+        M = beat.shape[0]
+        _check(self._lib.sar_form_image_host(self._plan, _ptr(beat), M, _ptr(w_az), _ptr(q_tx),
+                                             _ptr(q_rx), _ptr(image), _stream(stream)),
+               "sar_form_image_host")
+        return image
+
+    def check_errors(self) -> int:
+        return self._lib.sar_plan_check_errors(self._plan)

@@ -1,0 +1,633 @@
+// Host side of the C ABI declared in include/sar.h: parameter validation,
+// FP64 tables, pixel tiling, device memory and kernel launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "sar_internal.h"
+
+using namespace sar;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr size_t kBpSmemTarget = 110 * 1024;  // two CTAs per SM
+constexpr size_t kBpSmemMax = 227 * 1024;
+constexpr int kMaxPulsesPerBlock = 32;
+
+}  // namespace
+
+struct sar_plan {
+    sar_radar_params p{};
+    int device = 0;
+    int n_fft = 0, log2n = 0, crop_lo = 0, crop_hi = 0, n_bins = 0;
+    double a1 = 0, beta = 0;
+    int sign = 1;
+    bool fp16 = false;
+    int64_t n_pixels = 0;
+    int n_tiles = 0;
+    int L = 0, Mb = 0, rg = 1;
+    size_t bp_smem = 0;
+    int num_sms = 0, ctas_per_sm = 0, G = 0, seg_cap = 0;
+    float fd_max = 0.f;
+    // device memory owned by the plan
+    float *d_wr = nullptr;
+    float2 *d_tw = nullptr;
+    float2 *d_rot = nullptr;
+    float2 *d_pix = nullptr;
+    int *d_out = nullptr;
+    TileInfo *d_tiles = nullptr;
+    float2 *d_partial = nullptr;
+    int *d_err = nullptr;
+    // staging buffers of sar_form_image_host
+    void *s_beat = nullptr;
+    float *s_waz = nullptr;
+    double *s_qtx = nullptr, *s_qrx = nullptr;
+    void *s_prof = nullptr, *s_img = nullptr;
+    size_t budget = 0, used = 0;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int old = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&old) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (old != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (old >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != old) cudaSetDevice(old);
+    }
+};
+
+int dev_alloc(sar_plan *pl, size_t bytes, void **out) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (pl->budget && pl->used + bytes > pl->budget) return SAR_ENOMEM;
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SAR_ENOMEM;
+    }
+    pl->used += bytes;
+    pl->allocs.push_back(p);
+    *out = p;
+    return SAR_OK;
+}
+
+template <class T>
+int upload(sar_plan *pl, const std::vector<T> &h, T **out) {
+    void *p = nullptr;
+    int rc = dev_alloc(pl, h.size() * sizeof(T), &p);
+    if (rc) return rc;
+    if (!h.empty() && cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SAR_ECUDA;
+    *out = static_cast<T *>(p);
+    return SAR_OK;
+}
+
+void free_plan(sar_plan *pl) {
+    if (!pl) return;
+    DeviceGuard g(pl->device);
+    cudaDeviceSynchronize();
+    for (void *p : pl->allocs) cudaFree(p);
+    delete pl;
+}
+
+// Modified Bessel I0 from its power series.
+double i0_series(double x) {
+    double term = 1.0, sum = 1.0;
+    const double h = x / 2.0;
+    for (int k = 1; k < 1000; ++k) {
+        term *= h / k;
+        const double t2 = term * term;
+        sum += t2;
+        if (t2 <= sum * 1e-17) break;
+    }
+    return sum;
+}
+
+std::vector<float> range_window(int kind, int N, double beta) {
+    std::vector<float> w(N, 1.0f);
+    if (N == 1 || kind == SAR_WINDOW_RECT) return w;
+    for (int n = 0; n < N; ++n) {
+        double v = 1.0;
+        if (kind == SAR_WINDOW_HANN) {
+            v = 0.5 * (1.0 - std::cos(2.0 * kPi * n / (N - 1)));
+        } else {
+            const double t = 2.0 * n / (N - 1) - 1.0;
+            v = i0_series(beta * std::sqrt(std::max(0.0, 1.0 - t * t))) / i0_series(beta);
+        }
+        w[n] = (float)v;
+    }
+    return w;
+}
+
+int ilog2_exact(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return (1 << l) == n ? l : -1;
+}
+
+uint32_t spread_bits(uint32_t v) {
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+struct HostTiles {
+    std::vector<float2> pix;
+    std::vector<int> out;
+    std::vector<TileInfo> tiles;
+    double rho_max = 0;
+};
+
+void finish_tile(HostTiles &ht, int t, const std::vector<double> &xs, const std::vector<double> &ys,
+                 const std::vector<int> &oi) {
+    TileInfo ti{};
+    if (xs.empty()) {
+        ht.tiles[t] = ti;
+        return;
+    }
+    const double xl = *std::min_element(xs.begin(), xs.end()), xh = *std::max_element(xs.begin(), xs.end());
+    const double yl = *std::min_element(ys.begin(), ys.end()), yh = *std::max_element(ys.begin(), ys.end());
+    ti.x = 0.5 * (xl + xh);
+    ti.y = 0.5 * (yl + yh);
+    double rho = 0;
+    for (size_t i = 0; i < xs.size(); ++i) rho = std::max(rho, std::hypot(xs[i] - ti.x, ys[i] - ti.y));
+    ti.rho = rho * (1.0 + 1e-9) + 1e-9;
+    ti.n_valid = (int)xs.size();
+    ht.tiles[t] = ti;
+    ht.rho_max = std::max(ht.rho_max, ti.rho);
+    for (size_t i = 0; i < xs.size(); ++i) {
+        // slot i of the tile
+        const size_t s = (size_t)t * kTilePx + i;
+        ht.pix[s] = make_float2((float)(xs[i] - ti.x), (float)(ys[i] - ti.y));
+        ht.out[s] = oi[i];
+    }
+}
+
+int build_tiles(const sar_grid *g, HostTiles &ht, int64_t *n_pixels) {
+    if (g->pixels_xy == nullptr) {
+        if (g->nx <= 0 || g->ny <= 0 || !std::isfinite(g->x0) || !std::isfinite(g->y0) ||
+            !std::isfinite(g->dx) || !std::isfinite(g->dy))
+            return SAR_EINVAL;
+        const int64_t np = (int64_t)g->nx * g->ny;
+        if (np > (int64_t)1 << 30) return SAR_EINVAL;
+        *n_pixels = np;
+        const int ntx = (g->nx + 31) / 32, nty = (g->ny + 31) / 32;
+        const int T = ntx * nty;
+        ht.pix.assign((size_t)T * kTilePx, make_float2(0.f, 0.f));
+        ht.out.assign((size_t)T * kTilePx, -1);
+        ht.tiles.assign(T, TileInfo{});
+        std::vector<double> xs, ys;
+        std::vector<int> oi;
+        for (int ty = 0; ty < nty; ++ty)
+            for (int tx = 0; tx < ntx; ++tx) {
+                const int t = ty * ntx + tx;
+                xs.clear();
+                ys.clear();
+                oi.clear();
+                // slot = ly * 32 + lx: thread t owns column t % 32, rows t / 32 + 8 j
+                std::vector<int> slot_of;
+                for (int ly = 0; ly < 32; ++ly)
+                    for (int lx = 0; lx < 32; ++lx) {
+                        const int ix = tx * 32 + lx, iy = ty * 32 + ly;
+                        const bool v = ix < g->nx && iy < g->ny;
+                        xs.push_back(v ? g->x0 + ix * g->dx : 0.0);
+                        ys.push_back(v ? g->y0 + iy * g->dy : 0.0);
+                        oi.push_back(v ? iy * g->nx + ix : -1);
+                    }
+                // reference and radius from the valid points only
+                std::vector<double> vx, vy;
+                std::vector<int> vo;
+                for (size_t i = 0; i < oi.size(); ++i)
+                    if (oi[i] >= 0) {
+                        vx.push_back(xs[i]);
+                        vy.push_back(ys[i]);
+                        vo.push_back(oi[i]);
+                    }
+                finish_tile(ht, t, vx, vy, vo);
+                // place points at their 2-D slots (finish_tile packed them)
+                const TileInfo &ti = ht.tiles[t];
+                for (int s = 0; s < kTilePx; ++s) {
+                    const size_t d = (size_t)t * kTilePx + s;
+                    if (oi[s] >= 0) {
+                        ht.pix[d] = make_float2((float)(xs[s] - ti.x), (float)(ys[s] - ti.y));
+                        ht.out[d] = oi[s];
+                    } else {
+                        ht.pix[d] = make_float2(0.f, 0.f);
+                        ht.out[d] = -1;
+                    }
+                }
+            }
+        return SAR_OK;
+    }
+    // explicit point list: Morton order, 1024 consecutive points per tile
+    const int64_t np = g->n_pixels;
+    if (np <= 0 || np > (int64_t)1 << 30) return SAR_EINVAL;
+    *n_pixels = np;
+    const double *xy = g->pixels_xy;
+    double xl = INFINITY, xh = -INFINITY, yl = INFINITY, yh = -INFINITY;
+    for (int64_t i = 0; i < np; ++i) {
+        const double x = xy[2 * i], y = xy[2 * i + 1];
+        if (!std::isfinite(x) || !std::isfinite(y)) return SAR_EINVAL;
+        xl = std::min(xl, x);
+        xh = std::max(xh, x);
+        yl = std::min(yl, y);
+        yh = std::max(yh, y);
+    }
+    const double sx = xh > xl ? 65535.0 / (xh - xl) : 0.0;
+    const double sy = yh > yl ? 65535.0 / (yh - yl) : 0.0;
+    std::vector<uint32_t> code(np);
+    for (int64_t i = 0; i < np; ++i) {
+        const uint32_t qx = (uint32_t)std::lround((xy[2 * i] - xl) * sx);
+        const uint32_t qy = (uint32_t)std::lround((xy[2 * i + 1] - yl) * sy);
+        code[i] = spread_bits(qx) | (spread_bits(qy) << 1);
+    }
+    std::vector<int64_t> order(np);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return code[a] < code[b]; });
+    const int T = (int)((np + kTilePx - 1) / kTilePx);
+    ht.pix.assign((size_t)T * kTilePx, make_float2(0.f, 0.f));
+    ht.out.assign((size_t)T * kTilePx, -1);
+    ht.tiles.assign(T, TileInfo{});
+    std::vector<double> xs, ys;
+    std::vector<int> oi;
+    for (int t = 0; t < T; ++t) {
+        xs.clear();
+        ys.clear();
+        oi.clear();
+        for (int64_t k = (int64_t)t * kTilePx; k < std::min(np, (int64_t)(t + 1) * kTilePx); ++k) {
+            xs.push_back(xy[2 * order[k]]);
+            ys.push_back(xy[2 * order[k] + 1]);
+            oi.push_back((int)order[k]);
+        }
+        finish_tile(ht, t, xs, ys, oi);
+    }
+    return SAR_OK;
+}
+
+int validate_params(const sar_radar_params *p) {
+    if (!p) return SAR_EINVAL;
+    if (!(p->f0 > 0) || !(p->slope != 0) || !(p->fs > 0) || !(p->c > 0)) return SAR_EINVAL;
+    if (!std::isfinite(p->f0) || !std::isfinite(p->slope) || !std::isfinite(p->fs) || !std::isfinite(p->c))
+        return SAR_EINVAL;
+    if (p->n_samples < 1 || p->os < 1 || p->n_rx < 1 || p->n_rx > 64 || p->max_pulses < 1) return SAR_EINVAL;
+    const long long nfft = (long long)p->n_samples * p->os;
+    if (nfft < 64 || nfft > 16384 || ilog2_exact((int)nfft) < 0) return SAR_EINVAL;
+    if (p->range_window < 0 || p->range_window > 2) return SAR_EINVAL;
+    if (p->precision != SAR_PREC_FP32 && p->precision != SAR_PREC_FP16) return SAR_EINVAL;
+    if (p->phase_sign != 1 && p->phase_sign != -1) return SAR_EINVAL;
+    if (p->crop_lo < 0 || p->crop_hi < 0) return SAR_EINVAL;
+    if (!(p->crop_lo == 0 && p->crop_hi == 0)) {
+        if (p->crop_lo >= p->crop_hi || p->crop_hi > nfft - 1) return SAR_EINVAL;
+    }
+    if (!(p->max_doppler_bins >= 0) || p->max_doppler_bins > 64) return SAR_EINVAL;
+    if (p->range_window == SAR_WINDOW_KAISER && !(p->kaiser_beta >= 0 && p->kaiser_beta < 100)) return SAR_EINVAL;
+    return SAR_OK;
+}
+
+int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t budget, sar_plan **out) {
+    int rc = validate_params(params);
+    if (rc) return rc;
+    if (!grid) return SAR_EINVAL;
+    sar_plan *pl = new (std::nothrow) sar_plan();
+    if (!pl) return SAR_ENOMEM;
+    pl->p = *params;
+    pl->budget = budget;
+    if (cudaGetDevice(&pl->device) != cudaSuccess) {
+        delete pl;
+        return SAR_ECUDA;
+    }
+    const sar_radar_params &p = pl->p;
+    pl->n_fft = p.n_samples * p.os;
+    pl->log2n = ilog2_exact(pl->n_fft);
+    pl->crop_lo = (p.crop_lo == 0 && p.crop_hi == 0) ? 0 : p.crop_lo;
+    pl->crop_hi = (p.crop_lo == 0 && p.crop_hi == 0) ? pl->n_fft - 1 : p.crop_hi;
+    pl->n_bins = pl->crop_hi - pl->crop_lo + 1;
+    pl->sign = p.phase_sign;
+    pl->fp16 = p.precision == SAR_PREC_FP16;
+    pl->a1 = p.slope * pl->n_fft / (p.c * p.fs);
+    if (!(pl->a1 > 0)) {
+        delete pl;
+        return SAR_EINVAL;
+    }
+    pl->beta = p.f0 / (p.c * pl->a1);
+    pl->fd_max = (float)p.max_doppler_bins;
+
+    HostTiles ht;
+    rc = build_tiles(grid, ht, &pl->n_pixels);
+    if (rc) {
+        delete pl;
+        return rc;
+    }
+    pl->n_tiles = (int)ht.tiles.size();
+
+    // staged window length: covers a1 * (d0 -+ 2 rho) -+ fd_max plus guards
+    const double span = 4.0 * ht.rho_max * pl->a1 + 2.0 * std::ceil(p.max_doppler_bins);
+    int L = (int)std::ceil(span) + 2 * kGuardBins + 4;
+    L = (L + 3) & ~3;
+    pl->L = L;
+    pl->rg = (p.n_rx % 4 == 0) ? 4 : (p.n_rx % 2 == 0) ? 2 : 1;
+    const size_t per_pulse = bp_smem_bytes(1, p.n_rx, L, pl->fp16);
+    int Mb = (int)std::min<size_t>(kMaxPulsesPerBlock, std::max<size_t>(1, kBpSmemTarget / per_pulse));
+    while (Mb > 1 && bp_smem_bytes(Mb, p.n_rx, L, pl->fp16) > kBpSmemTarget) --Mb;
+    pl->Mb = Mb;
+    pl->bp_smem = bp_smem_bytes(Mb, p.n_rx, L, pl->fp16);
+    if (pl->bp_smem > kBpSmemMax) {
+        delete pl;
+        return SAR_EINVAL;  // reconstruction points too spread out for one tile window
+    }
+
+    DeviceGuard dg(pl->device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, pl->device) != cudaSuccess) {
+        delete pl;
+        return SAR_ECUDA;
+    }
+    pl->num_sms = prop.multiProcessorCount;
+    if (bp_prepare(pl->fp16, pl->rg, pl->bp_smem) != cudaSuccess ||
+        bp_occupancy(pl->fp16, pl->rg, pl->bp_smem, &pl->ctas_per_sm) != 0 || pl->ctas_per_sm < 1) {
+        cudaGetLastError();
+        delete pl;
+        return SAR_ECUDA;
+    }
+    pl->G = pl->num_sms * pl->ctas_per_sm;
+    pl->seg_cap = pl->n_tiles / pl->G + 2;
+
+    // FP64 tables
+    std::vector<float> wr = range_window(p.range_window, p.n_samples, p.kaiser_beta);
+    std::vector<float2> tw(pl->n_fft);
+    for (int i = 0; i < pl->n_fft; ++i) {
+        const double ang = pl->sign * 2.0 * kPi * (double)i / pl->n_fft;
+        tw[i] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    std::vector<float2> rot(pl->n_bins);
+    for (int i = 0; i < pl->n_bins; ++i) {
+        const double k = (double)(pl->crop_lo + i);
+        double cyc = k * pl->beta;
+        cyc -= std::floor(cyc);
+        const double ang = pl->sign * 2.0 * kPi * cyc;
+        rot[i] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+
+    rc = upload(pl, wr, &pl->d_wr);
+    if (!rc) rc = upload(pl, tw, &pl->d_tw);
+    if (!rc) rc = upload(pl, rot, &pl->d_rot);
+    if (!rc) rc = upload(pl, ht.pix, &pl->d_pix);
+    if (!rc) rc = upload(pl, ht.out, &pl->d_out);
+    if (!rc) rc = upload(pl, ht.tiles, &pl->d_tiles);
+    if (!rc) {
+        void *q = nullptr;
+        rc = dev_alloc(pl, (size_t)pl->G * pl->seg_cap * kTilePx * sizeof(float2), &q);
+        pl->d_partial = (float2 *)q;
+    }
+    if (!rc) {
+        void *q = nullptr;
+        rc = dev_alloc(pl, sizeof(int) * 4, &q);
+        pl->d_err = (int *)q;
+        if (!rc && cudaMemset(q, 0, sizeof(int) * 4) != cudaSuccess) rc = SAR_ECUDA;
+    }
+    if (rc) {
+        free_plan(pl);
+        return rc;
+    }
+    *out = pl;
+    return SAR_OK;
+}
+
+size_t profile_bytes(const sar_plan *pl, int M) {
+    const size_t rows = (size_t)M * pl->p.n_rx;
+    if (pl->fp16) return ((rows * 4 + 255) & ~size_t(255)) + rows * pl->n_bins * 4;
+    return rows * pl->n_bins * 8;
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int rc_launch(sar_plan *pl, const void *beat, int M, const float *w_az, void *out, int mode, cudaStream_t s) {
+    RcArgs a{};
+    a.beat = (const float2 *)beat;
+    a.w_r = pl->d_wr;
+    a.tw = pl->d_tw;
+    a.rot = pl->d_rot;
+    a.w_az = w_az;
+    a.rows = (long long)M * pl->p.n_rx;
+    a.R = pl->p.n_rx;
+    a.N = pl->p.n_samples;
+    a.n_fft = pl->n_fft;
+    a.log2n = pl->log2n;
+    a.crop_lo = pl->crop_lo;
+    a.n_bins = pl->n_bins;
+    if (mode == kRcProfileF16) {
+        const size_t rows = (size_t)M * pl->p.n_rx;
+        a.scales = (float *)out;
+        a.out = (unsigned char *)out + ((rows * 4 + 255) & ~size_t(255));
+    } else {
+        a.out = out;
+    }
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return SAR_ECUDA;
+    return launch_range_compress(a, pl->sign, mode, s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
+}
+
+int bp_launch(sar_plan *pl, const void *prof, int M, const double *q_tx, const double *q_rx, const float *fd,
+              void *image, int accumulate, cudaStream_t s) {
+    BpArgs a{};
+    const size_t rows = (size_t)M * pl->p.n_rx;
+    if (pl->fp16) {
+        a.prof_scale = (const float *)prof;
+        a.prof = (const unsigned char *)prof + ((rows * 4 + 255) & ~size_t(255));
+    } else {
+        a.prof = prof;
+        a.prof_scale = nullptr;
+    }
+    a.q_tx = q_tx;
+    a.q_rx = q_rx;
+    a.fdopp = fd;
+    a.image = (float2 *)image;
+    a.partial = pl->d_partial;
+    a.err = pl->d_err;
+    a.pix = pl->d_pix;
+    a.out_idx = pl->d_out;
+    a.tiles = pl->d_tiles;
+    a.M = M;
+    a.R = pl->p.n_rx;
+    a.n_tiles = pl->n_tiles;
+    a.Mb = pl->Mb;
+    a.L = pl->L;
+    a.blocks_per_tile = (M + pl->Mb - 1) / pl->Mb;
+    a.units = (long long)pl->n_tiles * a.blocks_per_tile;
+    a.G = (int)std::min<long long>(pl->G, a.units);
+    const long long per = (a.units + a.G - 1) / a.G;
+    a.seg_max = (int)((per - 1) / a.blocks_per_tile) + 2;
+    a.n_bins = pl->n_bins;
+    a.crop_lo = pl->crop_lo;
+    a.crop_hi = pl->crop_hi;
+    a.accumulate = accumulate ? 1 : 0;
+    a.a1 = pl->a1;
+    a.a1f = (float)pl->a1;
+    a.two_pi_beta = (float)(pl->sign * 2.0 * kPi * pl->beta);
+    a.beta = (float)pl->beta;
+    a.sign = (float)pl->sign;
+    const double cb = -pl->sign * 2.0 * kPi * (pl->beta - std::floor(pl->beta));
+    a.cb = make_float2((float)std::cos(cb), (float)std::sin(cb));
+    a.fd_max = pl->fd_max;
+    if ((long long)a.G * a.seg_max > (long long)pl->G * pl->seg_cap) return SAR_EINVAL;  // cannot happen
+    BpLaunch l{pl->rg, pl->fp16, pl->bp_smem};
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return SAR_ECUDA;
+    return launch_backproject(a, l, s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sar_version(void) { return 100; }
+
+const char *sar_status_string(int st) {
+    switch (st) {
+        case SAR_OK: return "ok";
+        case SAR_EINVAL: return "invalid argument";
+        case SAR_ENOMEM: return "out of device memory or HBM budget";
+        case SAR_EAGAIN: return "not ready";
+        case SAR_ETIMEOUT: return "timed out";
+        case SAR_ECUDA: return "CUDA error";
+        case SAR_EBOUNDS: return "invalid geometry skipped";
+        case SAR_ENOTFOUND: return "unknown ticket";
+        default: return "unknown status";
+    }
+}
+
+int sar_plan_create(const sar_radar_params *params, const sar_grid *grid, size_t hbm_budget_bytes,
+                    sar_plan **out) {
+    if (!out) return SAR_EINVAL;
+    *out = nullptr;
+    try {
+        return plan_create(params, grid, hbm_budget_bytes, out);
+    } catch (const std::bad_alloc &) {
+        return SAR_ENOMEM;
+    } catch (...) {
+        return SAR_EINVAL;
+    }
+}
+
+void sar_plan_destroy(sar_plan *plan) { free_plan(plan); }
+
+int sar_plan_get_info(const sar_plan *pl, sar_plan_info *info) {
+    if (!pl || !info) return SAR_EINVAL;
+    sar_plan_info i{};
+    i.n_fft = pl->n_fft;
+    i.n_bins = pl->n_bins;
+    i.crop_lo = pl->crop_lo;
+    i.crop_hi = pl->crop_hi;
+    i.n_pixels = pl->n_pixels;
+    i.n_tiles = pl->n_tiles;
+    i.window_bins = pl->L;
+    i.pulses_per_block = pl->Mb;
+    i.bp_ctas = pl->G;
+    i.bins_per_metre = pl->a1;
+    i.cycles_per_bin = pl->beta;
+    i.device_bytes = pl->used;
+    *info = i;
+    return SAR_OK;
+}
+
+int sar_profile_bytes(const sar_plan *pl, int32_t M, size_t *bytes) {
+    if (!pl || !bytes || M < 1 || M > pl->p.max_pulses) return SAR_EINVAL;
+    *bytes = profile_bytes(pl, M);
+    return SAR_OK;
+}
+
+int sar_range_compress(sar_plan *pl, const void *beat_dev, int32_t M, const float *w_az_dev, void *prof_dev,
+                       void *stream) {
+    if (!pl || !beat_dev || !prof_dev || M < 1 || M > pl->p.max_pulses) return SAR_EINVAL;
+    if (!aligned(beat_dev, 8) || !aligned(prof_dev, 256) || (w_az_dev && !aligned(w_az_dev, 4))) return SAR_EINVAL;
+    return rc_launch(pl, beat_dev, M, w_az_dev, prof_dev, pl->fp16 ? kRcProfileF16 : kRcProfileF32,
+                     (cudaStream_t)stream);
+}
+
+int sar_range_spectrum(sar_plan *pl, const void *beat_dev, int32_t M, void *spec_dev, void *stream) {
+    if (!pl || !beat_dev || !spec_dev || M < 1 || M > pl->p.max_pulses) return SAR_EINVAL;
+    if (!aligned(beat_dev, 8) || !aligned(spec_dev, 8)) return SAR_EINVAL;
+    return rc_launch(pl, beat_dev, M, nullptr, spec_dev, kRcSpectrum, (cudaStream_t)stream);
+}
+
+int sar_backproject(sar_plan *pl, const void *prof_dev, int32_t M, const double *q_tx_dev,
+                    const double *q_rx_dev, const float *fdopp_idx_dev, void *image_dev, int32_t accumulate,
+                    void *stream) {
+    if (!pl || !prof_dev || !q_tx_dev || !q_rx_dev || !image_dev || M < 1 || M > pl->p.max_pulses)
+        return SAR_EINVAL;
+    if (!aligned(prof_dev, 256) || !aligned(q_tx_dev, 16) || !aligned(q_rx_dev, 16) || !aligned(image_dev, 8) ||
+        (fdopp_idx_dev && !aligned(fdopp_idx_dev, 4)))
+        return SAR_EINVAL;
+    if (fdopp_idx_dev && !(pl->fd_max > 0)) return SAR_EINVAL;
+    return bp_launch(pl, prof_dev, M, q_tx_dev, q_rx_dev, fdopp_idx_dev, image_dev, accumulate,
+                     (cudaStream_t)stream);
+}
+
+int sar_form_image_host(sar_plan *pl, const void *beat_host, int32_t M, const float *w_az_host,
+                        const double *q_tx_host, const double *q_rx_host, void *image_host, void *stream) {
+    if (!pl || !beat_host || !q_tx_host || !q_rx_host || !image_host || M < 1 || M > pl->p.max_pulses)
+        return SAR_EINVAL;
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return SAR_ECUDA;
+    const int R = pl->p.n_rx, N = pl->p.n_samples, Mc = pl->p.max_pulses;
+    int rc = SAR_OK;
+    if (!pl->s_beat) {
+        void *q;
+        rc = dev_alloc(pl, (size_t)Mc * R * N * 8, &q);
+        if (!rc) pl->s_beat = q;
+        if (!rc) rc = dev_alloc(pl, (size_t)Mc * 4, &q), pl->s_waz = (float *)q;
+        if (!rc) rc = dev_alloc(pl, (size_t)Mc * 16, &q), pl->s_qtx = (double *)q;
+        if (!rc) rc = dev_alloc(pl, (size_t)Mc * R * 16, &q), pl->s_qrx = (double *)q;
+        if (!rc) rc = dev_alloc(pl, profile_bytes(pl, Mc), &q), pl->s_prof = q;
+        if (!rc) rc = dev_alloc(pl, (size_t)pl->n_pixels * 8, &q), pl->s_img = q;
+        if (rc) {
+            pl->s_beat = nullptr;  // partially allocated buffers stay owned by the plan
+            return rc;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    bool ok = cudaMemcpyAsync(pl->s_beat, beat_host, (size_t)M * R * N * 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    if (w_az_host)
+        ok = ok && cudaMemcpyAsync(pl->s_waz, w_az_host, (size_t)M * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(pl->s_qtx, q_tx_host, (size_t)M * 16, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(pl->s_qrx, q_rx_host, (size_t)M * R * 16, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    if (!ok) return SAR_ECUDA;
+    rc = rc_launch(pl, pl->s_beat, M, w_az_host ? pl->s_waz : nullptr, pl->s_prof,
+                   pl->fp16 ? kRcProfileF16 : kRcProfileF32, s);
+    if (rc) return rc;
+    rc = bp_launch(pl, pl->s_prof, M, pl->s_qtx, pl->s_qrx, nullptr, pl->s_img, 0, s);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(image_host, pl->s_img, (size_t)pl->n_pixels * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SAR_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
+}
+
+int sar_plan_check_errors(sar_plan *pl) {
+    if (!pl) return SAR_EINVAL;
+    DeviceGuard dg(pl->device);
+    if (cudaDeviceSynchronize() != cudaSuccess) return SAR_ECUDA;
+    int h[4] = {0, 0, 0, 0};
+    if (cudaMemcpy(h, pl->d_err, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return SAR_ECUDA;
+    if (cudaMemset(pl->d_err, 0, sizeof(h)) != cudaSuccess) return SAR_ECUDA;
+    return h[0] ? SAR_EBOUNDS : SAR_OK;
+}
+
+}  // extern "C"

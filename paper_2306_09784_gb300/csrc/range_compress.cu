@@ -1,0 +1,248 @@
+// Range compression: window, zero-padded range transform and profile store
+// for every (chirp, Rx) row of the FMCW beat cube.
+//
+// The paper interpolates the beat spectrum on an equidistant beat-frequency
+// axis (s(f_hyp) in Alg. 1, s(f_ind) in Alg. 2, Sec. III-C) but does not say how it is
+// produced; here it is the windowed, zero-padded DFT of each chirp,
+//     S[k] = sum_{n<N} w_r[n] beat[n] exp(sign j 2 pi n k / N_fft).
+//
+// One CTA transforms 4096 / N_fft rows (one row when N_fft >= 4096) in shared
+// memory.  Each thread keeps 16 values in registers; log2(N_fft) / 4 radix-16
+// Stockham passes (plus one radix-2/4/8 pass for the remainder) exchange
+// through one shared buffer.  The first pass reads the beat samples straight
+// from global memory with the range window fused into the load (zero padding
+// costs no loads).  The store stage folds w_sar[m] and the per-bin phase
+// rotation into the profile (see sar.h) and writes only the cropped bins.
+#include <cuda_fp16.h>
+
+#include "sar_internal.h"
+
+namespace sar {
+namespace {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// exp(SGN j 2 pi t / 16), t in [0, 8): exact values of cos/sin at multiples of pi/8.
+template <int SGN>
+__device__ __forceinline__ float2 w16(int t) {
+    constexpr float c1 = 0.923879532511286756f;  // cos(pi/8)
+    constexpr float s1 = 0.382683432365089772f;  // sin(pi/8)
+    constexpr float h = 0.707106781186547524f;   // cos(pi/4)
+    float c, s;
+    switch (t) {
+        case 0: c = 1.f; s = 0.f; break;
+        case 1: c = c1; s = s1; break;
+        case 2: c = h; s = h; break;
+        case 3: c = s1; s = c1; break;
+        case 4: c = 0.f; s = 1.f; break;
+        case 5: c = -s1; s = c1; break;
+        case 6: c = -h; s = h; break;
+        default: c = -c1; s = s1; break;
+    }
+    return make_float2(c, SGN > 0 ? s : -s);
+}
+
+template <int SGN>
+__device__ __forceinline__ float2 twiddle_const(float2 v, int t) {
+    if (t == 0) return v;
+    if (t == 4) return SGN > 0 ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+    return cmul(v, w16<SGN>(t));
+}
+
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+
+template <int RAD>
+__host__ __device__ constexpr int ilog2(int) {
+    return RAD == 2 ? 1 : RAD == 4 ? 2 : RAD == 8 ? 3 : 4;
+}
+
+// In-register DFT of RAD points, v[k] <- sum_n v[n] exp(SGN j 2 pi n k / RAD),
+// natural order in and out (radix-2 decimation in time).
+template <int RAD, int SGN>
+__device__ __forceinline__ void dft_reg(float2 *v) {
+    constexpr int bits = ilog2<RAD>(0);
+#pragma unroll
+    for (int i = 0; i < RAD; ++i) {
+        const int j = bitrev(i, bits);
+        if (i < j) {
+            float2 t = v[i];
+            v[i] = v[j];
+            v[j] = t;
+        }
+    }
+#pragma unroll
+    for (int h = 1; h < RAD; h <<= 1) {
+#pragma unroll
+        for (int s = 0; s < RAD; s += 2 * h) {
+#pragma unroll
+            for (int t = 0; t < h; ++t) {
+                const float2 a = v[s + t];
+                const float2 b = twiddle_const<SGN>(v[s + t + h], t * (8 / h));
+                v[s + t] = cadd(a, b);
+                v[s + t + h] = csub(a, b);
+            }
+        }
+    }
+}
+
+// One Stockham pass of radix RAD over an n-point row held in shared memory X
+// (Ns = product of the radices of the earlier passes).  Each of the T = n/16
+// threads of the row owns 16 values: 16/RAD butterflies j = tid + g T.
+// FIRST: the pass reads the windowed beat samples from global memory.
+template <int RAD, int SGN, bool FIRST>
+__device__ __forceinline__ void stockham_pass(float2 *X, int n, int log2n, int Ns, int tid, int T,
+                                              bool active, const float2 *__restrict__ tw,
+                                              const float2 *__restrict__ beat_row,
+                                              const float *__restrict__ w_r, int N) {
+    constexpr int G = 16 / RAD;
+    const int stride = n / RAD;
+    float2 v[16];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int j = tid + g * T;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) {
+            const int idx = j + r * stride;
+            if (FIRST) {
+                float2 x = make_float2(0.f, 0.f);
+                if (active && idx < N) {
+                    const float2 b = __ldg(beat_row + idx);
+                    const float w = __ldg(w_r + idx);
+                    x = make_float2(w * b.x, w * b.y);
+                }
+                v[g * RAD + r] = x;
+            } else {
+                v[g * RAD + r] = X[idx];
+            }
+        }
+    }
+    if (!FIRST) __syncthreads();
+    // log2(n / (Ns * RAD)): shift from the twiddle exponent k r to the table index
+    const int tw_shift = log2n - (31 - __clz(Ns)) - ilog2<RAD>(0);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int j = tid + g * T;
+        const int k = j & (Ns - 1);
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < RAD; ++r) {
+                v[g * RAD + r] = cmul(v[g * RAD + r], __ldg(tw + ((k * r) << tw_shift)));
+            }
+        }
+        dft_reg<RAD, SGN>(v + g * RAD);
+        const int base = (j - k) * RAD + k;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) X[base + r * Ns] = v[g * RAD + r];
+    }
+    __syncthreads();
+}
+
+template <int SGN, int MODE>
+__global__ void __launch_bounds__(1024) range_compress_kernel(RcArgs a) {
+    extern __shared__ float2 smem_rc[];
+    __shared__ int row_max[64];  // rows per CTA <= 4096 / 64
+    const int n = a.n_fft;
+    const int T = n >> 4;
+    const int rows_per_cta = blockDim.x / T;
+    const int lrow = threadIdx.x / T;
+    const int tid = threadIdx.x - lrow * T;
+    const long long row = (long long)blockIdx.x * rows_per_cta + lrow;
+    const bool active = row < a.rows;
+    float2 *X = smem_rc + (size_t)lrow * n;
+    const float2 *beat_row = a.beat + (active ? row : 0) * (long long)a.N;
+
+    if (MODE == kRcProfileF16 && threadIdx.x < 64) row_max[threadIdx.x] = 0;
+
+    // radix-16 passes, then the remainder radix
+    const int n16 = a.log2n >> 2;
+    const int rem = a.log2n & 3;
+    int Ns = 1;
+    for (int p = 0; p < n16; ++p) {
+        if (p == 0)
+            stockham_pass<16, SGN, true>(X, n, a.log2n, Ns, tid, T, active, a.tw, beat_row, a.w_r, a.N);
+        else
+            stockham_pass<16, SGN, false>(X, n, a.log2n, Ns, tid, T, active, a.tw, beat_row, a.w_r, a.N);
+        Ns <<= 4;
+    }
+    if (rem == 1) stockham_pass<2, SGN, false>(X, n, a.log2n, Ns, tid, T, active, a.tw, beat_row, a.w_r, a.N);
+    if (rem == 2) stockham_pass<4, SGN, false>(X, n, a.log2n, Ns, tid, T, active, a.tw, beat_row, a.w_r, a.N);
+    if (rem == 3) stockham_pass<8, SGN, false>(X, n, a.log2n, Ns, tid, T, active, a.tw, beat_row, a.w_r, a.N);
+
+    if (MODE == kRcSpectrum) {
+        if (!active) return;
+        float2 *out = reinterpret_cast<float2 *>(a.out) + row * (long long)n;
+        for (int k = tid; k < n; k += T) out[k] = X[k];
+        return;
+    }
+
+    const float g = (a.w_az != nullptr && active) ? __ldg(a.w_az + row / a.R) : 1.f;
+    if (MODE == kRcProfileF32) {
+        if (!active) return;
+        float2 *out = reinterpret_cast<float2 *>(a.out) + row * (long long)a.n_bins;
+        for (int i = tid; i < a.n_bins; i += T) {
+            const float2 v = cmul(X[a.crop_lo + i], __ldg(a.rot + i));
+            out[i] = make_float2(g * v.x, g * v.y);
+        }
+        return;
+    }
+
+    // FP16 profile: per-row max |component| sets the scale (max maps to 2^14)
+    float mx = 0.f;
+    if (active) {
+        for (int i = tid; i < a.n_bins; i += T) {
+            const float2 v = cmul(X[a.crop_lo + i], __ldg(a.rot + i));
+            mx = fmaxf(mx, fmaxf(fabsf(g * v.x), fabsf(g * v.y)));
+        }
+    }
+    atomicMax(&row_max[lrow], __float_as_int(mx));
+    __syncthreads();
+    if (!active) return;
+    const float rmax = __int_as_float(row_max[lrow]);
+    const float scale = rmax > 0.f ? rmax * (1.0f / 16384.0f) : 1.0f;
+    const float inv = 1.0f / scale;
+    if (tid == 0) a.scales[row] = scale;
+    __half2 *out = reinterpret_cast<__half2 *>(a.out) + row * (long long)a.n_bins;
+    for (int i = tid; i < a.n_bins; i += T) {
+        const float2 v = cmul(X[a.crop_lo + i], __ldg(a.rot + i));
+        out[i] = __floats2half2_rn(g * v.x * inv, g * v.y * inv);
+    }
+}
+
+template <int SGN, int MODE>
+cudaError_t launch_rc(const RcArgs &a, cudaStream_t s) {
+    const int n = a.n_fft;
+    const int T = n / 16;
+    const int rows_per_cta = n >= 4096 ? 1 : 4096 / n;
+    const int threads = T * rows_per_cta;
+    const size_t smem = (size_t)rows_per_cta * n * sizeof(float2);
+    auto kern = range_compress_kernel<SGN, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long blocks = (a.rows + rows_per_cta - 1) / rows_per_cta;
+    if (blocks == 0) return cudaSuccess;
+    kern<<<(unsigned)blocks, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_range_compress(const RcArgs &a, int sign, int mode, cudaStream_t s) {
+    if (sign > 0) {
+        if (mode == kRcProfileF32) return launch_rc<1, kRcProfileF32>(a, s);
+        if (mode == kRcProfileF16) return launch_rc<1, kRcProfileF16>(a, s);
+        return launch_rc<1, kRcSpectrum>(a, s);
+    }
+    if (mode == kRcProfileF32) return launch_rc<-1, kRcProfileF32>(a, s);
+    if (mode == kRcProfileF16) return launch_rc<-1, kRcProfileF16>(a, s);
+    return launch_rc<-1, kRcSpectrum>(a, s);
+}
+
+}  // namespace sar

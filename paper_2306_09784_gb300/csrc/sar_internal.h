@@ -1,0 +1,91 @@
+// Internal declarations shared by the host API (api.cpp) and the CUDA
+// kernels (range_compress.cu, backproject.cu).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sar.h"
+
+namespace sar {
+
+// Backprojection tiling: 1024 reconstruction points per tile, 256 threads,
+// 4 points per thread.
+constexpr int kTilePx = 1024;
+constexpr int kBpThreads = 256;
+constexpr int kPxPerThread = kTilePx / kBpThreads;
+// Bins of guard band on each side of a staged window.
+constexpr int kGuardBins = 2;
+// Absolute distances beyond this (m) are treated as invalid geometry.
+constexpr double kMaxRange = 1.0e6;
+
+// Range compression output modes.
+enum RcMode { kRcProfileF32 = 0, kRcProfileF16 = 1, kRcSpectrum = 2 };
+
+struct RcArgs {
+    const float2 *beat;      // [rows][N]
+    const float *w_r;        // [N] range window
+    const float2 *tw;        // [n_fft] exp(sign j 2 pi i / n_fft)
+    const float2 *rot;       // [n_bins] exp(sign j 2 pi frac(k beta)), k = crop_lo + i
+    const float *w_az;       // [M] or null
+    void *out;               // profile samples or spectrum
+    float *scales;           // [rows] (FP16 profiles)
+    long long rows;          // M * R
+    int R;
+    int N;
+    int n_fft;
+    int log2n;
+    int crop_lo;
+    int n_bins;
+};
+
+cudaError_t launch_range_compress(const RcArgs &a, int sign, int mode, cudaStream_t s);
+
+// Per-tile data: reference point (x, y), radius rho (max distance of the
+// tile's points from the reference), number of valid points.
+struct TileInfo {
+    double x, y, rho;
+    int32_t n_valid;
+    int32_t pad;
+};
+
+struct BpArgs {
+    const void *prof;          // profile samples (float2 or half2)
+    const float *prof_scale;   // [M][R] FP16 scales, or null
+    const double *q_tx;        // [M][2]
+    const double *q_rx;        // [M][R][2]
+    const float *fdopp;        // [n_pixels] or null
+    float2 *image;             // [n_pixels]
+    float2 *partial;           // [G * seg_max][kTilePx]
+    int *err;                  // device error flags
+    const float2 *pix;         // [n_tiles][kTilePx] (dx, dy) from the tile reference
+    const int *out_idx;        // [n_tiles][kTilePx] image index or -1
+    const TileInfo *tiles;     // [n_tiles]
+    long long units;           // n_tiles * blocks_per_tile
+    int G;                     // persistent CTAs
+    int blocks_per_tile;       // ceil(M / Mb)
+    int seg_max;               // partial slots per CTA
+    int M, R, n_tiles, Mb, L;
+    int n_bins, crop_lo, crop_hi;
+    int accumulate;
+    double a1;                 // bins per metre
+    float a1f;
+    float two_pi_beta;         // sign * 2 pi beta (radians per bin)
+    float beta;                // cycles per bin
+    float sign;
+    float2 cb;                 // exp(-sign j 2 pi beta)
+    float fd_max;              // bound on |f_doppler|
+};
+
+struct BpLaunch {
+    int rg;       // Rx group size of the inner loop (1, 2 or 4)
+    bool fp16;
+    size_t smem;  // dynamic shared memory bytes
+};
+
+size_t bp_smem_bytes(int Mb, int R, int L, bool fp16);
+cudaError_t bp_prepare(bool fp16, int rg, size_t smem);  // sets function attributes
+int bp_occupancy(bool fp16, int rg, size_t smem, int *ctas_per_sm);
+cudaError_t launch_backproject(const BpArgs &a, const BpLaunch &l, cudaStream_t s);
+
+}  // namespace sar

@@ -7,7 +7,7 @@ transform, no interpolation, no backprojection).  The FP64 oracle and the CUDA
 library both consume the arrays made here, so that parity tests compare the
 two on identical inputs.
 
-Radar model (paper Table I and Sec. II; the readings are listed in the design doc):
+Radar model (paper Table I and Sec. II, plus readings where the paper is silent):
 
 * FMCW chirp of slope ``mu = B / T_P`` starting at ``f0`` at sample 0;
   ``fs = N / T_P``.
@@ -286,6 +286,7 @@ def beat_signal(radar: Radar, q_tx: np.ndarray, q_rx: np.ndarray,
         qr = torch.as_tensor(q_rx, dtype=f64, device=dev)
         tt = torch.as_tensor(t, dtype=f64, device=dev)
         acc = torch.zeros((M, R, N), dtype=torch.complex128, device=dev)
+        chunk = max(1, min(256, int(4e8 // (M * R * N))))
         for k0 in range(0, len(targets), chunk):
             tk = torch.as_tensor(targets[k0:k0 + chunk], dtype=f64, device=dev)
             ak = torch.as_tensor(amps[k0:k0 + chunk], dtype=torch.complex128, device=dev)

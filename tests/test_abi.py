@@ -1,0 +1,106 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/sar.h declares; the Python structs match the C layout.  No GPU
+needed (no compute calls)."""
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sar.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sar_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2306_09784_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ("sar_plan_create", "sar_range_compress", "sar_backproject", "sar_plan_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_binding_lists_every_declared_symbol():
+    import paper_2306_09784_gb300 as sar
+    assert sorted(sar.EXPORTS) == declared_functions()
+
+
+def test_status_strings(lib):
+    lib.sar_status_string.restype = ctypes.c_char_p
+    assert lib.sar_status_string(0) == b"ok"
+    assert lib.sar_status_string(2).startswith(b"out of device memory")
+    lib.sar_version.restype = ctypes.c_int
+    assert lib.sar_version() >= 100
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    """Argument checks run on the host before any CUDA call."""
+    lib.sar_plan_create.restype = ctypes.c_int
+    assert lib.sar_plan_create(None, None, 0, None) == 1
+    out = ctypes.c_void_p()
+    assert lib.sar_plan_create(None, None, 0, ctypes.byref(out)) == 1
+    for fn in ("sar_range_compress", "sar_backproject", "sar_profile_bytes",
+               "sar_plan_get_info", "sar_plan_check_errors"):
+        getattr(lib, fn).restype = ctypes.c_int
+    assert lib.sar_range_compress(None, None, 1, None, None, None) == 1
+    assert lib.sar_backproject(None, None, 1, None, None, None, None, 0, None) == 1
+    assert lib.sar_plan_check_errors(None) == 1
+
+
+def test_struct_layouts_match_header():
+    import paper_2306_09784_gb300 as sar
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not available")
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "sar.h"
+#define P(T, F) printf(#T "." #F " %zu\n", offsetof(T, F));
+int main(void) {
+  printf("sar_radar_params %zu\nsar_grid %zu\nsar_plan_info %zu\n",
+         sizeof(sar_radar_params), sizeof(sar_grid), sizeof(sar_plan_info));
+  P(sar_radar_params, kaiser_beta) P(sar_radar_params, phase_sign) P(sar_radar_params, max_doppler_bins)
+  P(sar_grid, pixels_xy) P(sar_grid, n_pixels)
+  P(sar_plan_info, n_pixels) P(sar_plan_info, bins_per_metre) P(sar_plan_info, device_bytes)
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as td:
+        src = os.path.join(td, "t.c")
+        open(src, "w").write(prog)
+        exe = os.path.join(td, "t")
+        subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        lines = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(l.rsplit(" ", 1) for l in lines if l)
+    assert int(got["sar_radar_params"]) == ctypes.sizeof(sar.RadarParams)
+    assert int(got["sar_grid"]) == ctypes.sizeof(sar.Grid)
+    assert int(got["sar_plan_info"]) == ctypes.sizeof(sar.PlanInfo)
+    assert int(got["sar_radar_params.kaiser_beta"]) == sar.RadarParams.kaiser_beta.offset
+    assert int(got["sar_radar_params.phase_sign"]) == sar.RadarParams.phase_sign.offset
+    assert int(got["sar_radar_params.max_doppler_bins"]) == sar.RadarParams.max_doppler_bins.offset
+    assert int(got["sar_grid.pixels_xy"]) == sar.Grid.pixels_xy.offset
+    assert int(got["sar_grid.n_pixels"]) == sar.Grid.n_pixels.offset
+    assert int(got["sar_plan_info.n_pixels"]) == sar.PlanInfo.n_pixels.offset
+    assert int(got["sar_plan_info.bins_per_metre"]) == sar.PlanInfo.bins_per_metre.offset
+    assert int(got["sar_plan_info.device_bytes"]) == sar.PlanInfo.device_bytes.offset

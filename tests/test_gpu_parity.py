@@ -1,0 +1,405 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_helpers import (TOL_FP16, TOL_FP32, beta_of, check_peaks, gpu_image, make_plan,
+                               oracle_image, peak_windows, rel_l2, rotation, sample_pixels,
+                               to_dev)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    import paper_2306_09784_gb300 as sar
+    sar.load_library()  # fails loudly when the library is missing
+    return t
+
+
+@pytest.fixture(scope="module")
+def small():
+    wl = synth.make_workload("small")
+    return wl, synth.workload_beat(wl), np.hanning(wl.n_pulses)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    wl = synth.make_workload("tiny")
+    return wl, synth.workload_beat(wl), np.hanning(wl.n_pulses)
+
+
+# ----------------------------------------------------------------------------
+# range compression
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("os_factor,N", [(4, 128), (1, 64), (16, 64), (4, 4096), (2, 64)])
+def test_range_spectrum_vs_oracle(torch, os_factor, N):
+    radar = synth.Radar(n_samples=N, n_rx=3, os=os_factor)
+    rng = np.random.Generator(np.random.PCG64(N + os_factor))
+    M = 5
+    beat = (rng.standard_normal((M, 3, N)) + 1j * rng.standard_normal((M, 3, N))).astype(np.complex64)
+    grid = synth.Grid(0.0, 2.0, 0.05, 0.05, 4, 4)
+    import paper_2306_09784_gb300 as sar
+    plan = sar.Plan.from_radar(radar, max_pulses=M, grid=grid)
+    spec = plan.range_spectrum(torch.from_numpy(beat).cuda()).cpu().numpy()
+    ref = oracle.range_compress(beat, oracle.window(1, N), os_factor)
+    err = np.abs(spec - ref).max() / np.abs(ref).max()
+    assert err < 2e-6, err
+
+
+def test_range_spectrum_vs_cufft(torch, small):
+    """Cross-check against cuFFT (torch.fft.ifft, library call) of the
+    windowed, zero-padded rows."""
+    wl, beat, _ = small
+    plan = make_plan(wl)
+    b = torch.from_numpy(beat).cuda()
+    spec = plan.range_spectrum(b)
+    r = wl.radar
+    w = torch.from_numpy(np.hanning(r.n_samples).astype(np.float32)).cuda()
+    x = torch.zeros((wl.n_pulses, r.n_rx, r.n_fft), dtype=torch.complex64, device="cuda")
+    x[:, :, :r.n_samples] = b * w
+    ref = torch.fft.ifft(x, dim=-1) * r.n_fft
+    err = ((spec - ref).abs().max() / ref.abs().max()).item()
+    assert err < 2e-6, err
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_profile_vs_oracle(torch, small, precision):
+    """Stored profile = w_sar[m] rot[k] S[m][r][k] over the crop, FP32 or FP16
+    with a per-(chirp, Rx) scale."""
+    wl, beat, w_az = small
+    plan = make_plan(wl, precision=precision)
+    b, w, _, _ = to_dev(wl, beat, w_az)
+    prof = plan.range_compress(b, w).cpu().numpy()
+    M, R = wl.n_pulses, wl.radar.n_rx
+    lo, hi = wl.crop
+    nb = hi - lo + 1
+    S = oracle.range_compress(beat, oracle.window(1, wl.radar.n_samples), wl.radar.os)
+    ref = w_az[:, None, None] * rotation(wl.radar, wl.crop)[None, None, :] * S[:, :, lo:hi + 1]
+    if precision == 0:
+        got = prof.view(np.complex64).reshape(M, R, nb)
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err < 2e-6, err
+    else:
+        pad = (M * R * 4 + 255) // 256 * 256
+        scale = prof[:M * R * 4].view(np.float32).reshape(M, R)
+        h = prof[pad:pad + M * R * nb * 4].view(np.float16).reshape(M, R, nb, 2).astype(np.float64)
+        got = (h[..., 0] + 1j * h[..., 1]) * scale[..., None]
+        rowmax = np.abs(ref).max(axis=-1, keepdims=True)
+        err = (np.abs(got - ref) / rowmax).max()
+        assert err < 2e-3, err
+
+
+# ----------------------------------------------------------------------------
+# backprojection
+# ----------------------------------------------------------------------------
+def test_tiny_fp32(torch, tiny):
+    """Config 'tiny': full image vs oracle, rel L2 <= 1e-3, exact peak pixels."""
+    wl, beat, w_az = tiny
+    plan = make_plan(wl)
+    img = gpu_image(plan, wl, beat, w_az)
+    ref = oracle_image(wl, beat, w_az)
+    err = rel_l2(img, ref)
+    print(f"tiny fp32 rel L2 = {err:.3e}")
+    assert err <= TOL_FP32, err
+    assert check_peaks(img, ref, peak_windows(wl, n_peaks=5)) == []
+    assert plan.check_errors() == 0
+
+
+def test_tiny_fp16(torch, tiny):
+    wl, beat, w_az = tiny
+    plan = make_plan(wl, precision=1)
+    img = gpu_image(plan, wl, beat, w_az)
+    ref = oracle_image(wl, beat, w_az)
+    err = rel_l2(img, ref)
+    print(f"tiny fp16 rel L2 = {err:.3e}")
+    assert err <= TOL_FP16, err
+    assert check_peaks(img, ref, peak_windows(wl, n_peaks=5)) == []
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_small_multitile_ragged(torch, small, precision):
+    """80 x 72 pixels: several 32 x 32 tiles with ragged edges, 2 Rx."""
+    wl, beat, w_az = small
+    plan = make_plan(wl, precision=precision)
+    img = gpu_image(plan, wl, beat, w_az)
+    ref = oracle_image(wl, beat, w_az)
+    err = rel_l2(img, ref)
+    assert err <= (TOL_FP32 if precision == 0 else TOL_FP16), err
+
+
+def test_subaperture_accumulate(torch, small):
+    """BP over [0, M) = BP over [0, k) accumulated with BP over [k, M)."""
+    wl, beat, w_az = small
+    plan = make_plan(wl)
+    b, w, qt, qr = to_dev(wl, beat, w_az)
+    M, k = wl.n_pulses, 37
+    full = plan.backproject(plan.range_compress(b, w), M, qt, qr)
+    img = plan.backproject(plan.range_compress(b[:k].contiguous(), w[:k].contiguous()), k,
+                           qt[:k].contiguous(), qr[:k].contiguous())
+    plan.backproject(plan.range_compress(b[k:].contiguous(), w[k:].contiguous()), M - k,
+                     qt[k:].contiguous(), qr[k:].contiguous(), image=img, accumulate=True)
+    e = ((img - full).abs().norm() / full.abs().norm()).item()
+    assert e < 1e-5, e
+
+
+def test_linearity(torch, small):
+    wl, beat, w_az = small
+    rng = np.random.Generator(np.random.PCG64(99))
+    beat2 = (rng.standard_normal(beat.shape) + 1j * rng.standard_normal(beat.shape)).astype(np.complex64)
+    plan = make_plan(wl)
+    a = gpu_image(plan, wl, beat, w_az)
+    b = gpu_image(plan, wl, beat2, w_az)
+    s = gpu_image(plan, wl, (beat + beat2).astype(np.complex64), w_az)
+    assert rel_l2(a + b, s) < 1e-5
+
+
+def test_deterministic(torch, small):
+    wl, beat, w_az = small
+    plan = make_plan(wl)
+    a = gpu_image(plan, wl, beat, w_az)
+    b = gpu_image(plan, wl, beat, w_az)
+    assert np.array_equal(a, b)
+
+
+def test_translation_invariance(torch):
+    """Scene and trajectory offset by (1000 m, 1000 m): the FP64 per-tile
+    reference keeps the GPU image within tolerance of the oracle (a plain FP32
+    distance would lose the 77 GHz phase)."""
+    wl0 = synth.make_workload("small")
+    off = np.array([1000.0, 1000.0])
+    wl = synth.Workload(name="small+1km", radar=wl0.radar, n_pulses=wl0.n_pulses,
+                        grid=synth.Grid(wl0.grid.x0 + off[0], wl0.grid.y0 + off[1], wl0.grid.dx,
+                                        wl0.grid.dy, wl0.grid.nx, wl0.grid.ny),
+                        q_tx=wl0.q_tx + off, q_rx=wl0.q_rx + off, targets=wl0.targets + off,
+                        amps=wl0.amps, snr_db=wl0.snr_db, seed=wl0.seed, crop=wl0.crop)
+    beat = synth.workload_beat(wl)
+    w_az = np.hanning(wl.n_pulses)
+    plan = make_plan(wl)
+    img = gpu_image(plan, wl, beat, w_az)
+    ref = oracle_image(wl, beat, w_az)
+    assert rel_l2(img, ref) <= TOL_FP32
+
+
+@pytest.mark.parametrize("n_rx", [1, 2, 3, 4, 8])
+def test_rx_counts(torch, n_rx):
+    """Inner-loop Rx grouping (1, 2, 4) and ragged pulse blocks (M = 45)."""
+    radar = synth.Radar(n_samples=128, n_rx=n_rx, os=4)
+    M = 45
+    rng = np.random.Generator(np.random.PCG64(n_rx))
+    q_tx, q_rx = synth.trajectory(radar, M, jitter=0.01, rng=rng)
+    grid = synth.Grid(-0.8, 2.0, 0.04, 0.04, 40, 33)
+    tg = np.stack([rng.uniform(-0.7, 0.7, 6), rng.uniform(2.1, 3.2, 6)], 1)
+    am = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+    wl = synth.Workload("rx", radar, M, grid, q_tx, q_rx, tg, am, None, 0,
+                        synth.crop_for(radar, grid, q_tx, q_rx))
+    beat = synth.workload_beat(wl)
+    w_az = np.hanning(M)
+    img = gpu_image(make_plan(wl), wl, beat, w_az)
+    ref = oracle_image(wl, beat, w_az)
+    assert rel_l2(img, ref) <= TOL_FP32
+
+
+@pytest.mark.parametrize("os_factor", [1, 2, 8, 16])
+def test_zero_padding_factors(torch, os_factor):
+    radar = synth.Radar(n_samples=128 if os_factor < 16 else 256, n_rx=2, os=os_factor)
+    M = 40
+    q_tx, q_rx = synth.trajectory(radar, M)
+    grid = synth.Grid(-0.6, 2.5, 0.05, 0.05, 24, 24)
+    rng = np.random.Generator(np.random.PCG64(os_factor))
+    tg = np.stack([rng.uniform(-0.5, 0.5, 4), rng.uniform(2.6, 3.6, 4)], 1)
+    am = rng.standard_normal(4) + 1j * rng.standard_normal(4)
+    wl = synth.Workload("os", radar, M, grid, q_tx, q_rx, tg, am, 20.0, 1,
+                        synth.crop_for(radar, grid, q_tx, q_rx))
+    beat = synth.workload_beat(wl)
+    w_az = np.hanning(M)
+    img = gpu_image(make_plan(wl), wl, beat, w_az)
+    ref = oracle_image(wl, beat, w_az)
+    assert rel_l2(img, ref) <= TOL_FP32
+
+
+def test_full_crop_default(torch, small):
+    """crop (0, 0) = full valid range [0, N_fft - 1)."""
+    wl, beat, w_az = small
+    plan = make_plan(wl, crop=(0, 0))
+    img = gpu_image(plan, wl, beat, w_az)
+    ref = oracle_image(wl, beat, w_az, crop=(0, wl.radar.n_fft - 1))
+    assert rel_l2(img, ref) <= TOL_FP32
+
+
+def test_crop_cuts_geometry(torch, small):
+    """A crop narrower than the geometry: terms outside contribute nothing,
+    exactly as in the oracle."""
+    wl, beat, w_az = small
+    lo, hi = wl.crop
+    crop = (lo + (hi - lo) // 3, lo + 2 * (hi - lo) // 3)
+    plan = make_plan(wl, crop=crop)
+    img = gpu_image(plan, wl, beat, w_az)
+    ref = oracle_image(wl, beat, w_az, crop=crop)
+    assert rel_l2(img, ref) <= TOL_FP32
+
+
+def test_conjugate_convention(torch, small):
+    wl, beat, w_az = small
+    plan = make_plan(wl, phase_sign=-1)
+    bc = np.conj(beat).astype(np.complex64)
+    img = gpu_image(plan, wl, bc, w_az)
+    ref = oracle_image(wl, bc, w_az, sign=-1)
+    assert rel_l2(img, ref) <= TOL_FP32
+    ref_plus = oracle_image(wl, beat, w_az)
+    assert rel_l2(img, np.conj(ref_plus)) <= TOL_FP32
+
+
+def test_pixel_list_polar(torch, small):
+    """Explicit reconstruction points (a polar grid centred on the aperture,
+    Sec. III-E) in the caller's order."""
+    wl, beat, w_az = small
+    rr = np.arange(1.6, 4.8, 0.03)
+    th = np.deg2rad(np.arange(-35, 35, 0.6))
+    R_, T_ = np.meshgrid(rr, th, indexing="ij")
+    px = np.stack([R_.ravel() * np.sin(T_.ravel()), R_.ravel() * np.cos(T_.ravel())], 1)
+    perm = np.random.Generator(np.random.PCG64(3)).permutation(len(px))
+    px = px[perm]
+    plan = make_plan(wl, pixels_xy=px)
+    img = gpu_image(plan, wl, beat, w_az)
+    ref = oracle_image(wl, beat, w_az, px=px)
+    assert rel_l2(img, ref) <= TOL_FP32
+
+
+def test_single_pixel_single_pulse(torch):
+    radar = synth.Radar(n_samples=64, n_rx=1, os=4)
+    q_tx, q_rx = synth.trajectory(radar, 1)
+    grid = synth.Grid(0.1, 3.0, 0.05, 0.05, 1, 1)
+    wl = synth.Workload("one", radar, 1, grid, q_tx, q_rx, np.array([[0.1, 3.0]]),
+                        np.array([1.0 + 0.5j]), None, 0, synth.crop_for(radar, grid, q_tx, q_rx))
+    beat = synth.workload_beat(wl)
+    img = gpu_image(make_plan(wl), wl, beat, np.ones(1))
+    ref = oracle_image(wl, beat, np.ones(1))
+    assert abs(img[0] - ref[0]) <= 1e-4 * abs(ref[0])
+
+
+def test_doppler_offsets(torch, small):
+    """Per-pixel f_doppler(p) index offsets of Alg. 2 (phase from d_hyp)."""
+    wl, beat, w_az = small
+    rng = np.random.Generator(np.random.PCG64(5))
+    fd = rng.uniform(-1.5, 1.5, wl.grid.nx * wl.grid.ny)
+    plan = make_plan(wl, max_doppler_bins=2.0)
+    img = gpu_image(plan, wl, beat, w_az, fdopp=fd)
+    ref = oracle_image(wl, beat, w_az, fd_idx=fd.astype(np.float32).astype(np.float64))
+    assert rel_l2(img, ref) <= TOL_FP32
+
+
+def test_invalid_geometry_is_flagged(torch, small):
+    """A non-finite antenna position is skipped (no contribution) and
+    reported by sar_plan_check_errors; the rest of the image is unaffected."""
+    import paper_2306_09784_gb300 as sar
+    wl, beat, w_az = small
+    plan = make_plan(wl)
+    b, w, qt, qr = to_dev(wl, beat, w_az)
+    qt_bad = qt.clone()
+    qt_bad[5, 0] = float("nan")
+    img = plan.backproject(plan.range_compress(b, w), wl.n_pulses, qt_bad, qr)
+    assert plan.check_errors() == sar.SAR_EBOUNDS
+    assert plan.check_errors() == sar.SAR_OK
+    keep = np.ones(wl.n_pulses, bool)
+    keep[5] = False
+    wk = w_az.copy()
+    wk[5] = 0.0
+    ref = oracle_image(wl, beat, wk)
+    assert np.isfinite(img.cpu().numpy()).all()
+    assert rel_l2(img.cpu().numpy(), ref) <= TOL_FP32
+
+
+def test_host_entry_point(torch, small):
+    """sar_form_image_host (host buffers, copies inside) = the device path."""
+    wl, beat, w_az = small
+    plan = make_plan(wl)
+    dev = gpu_image(plan, wl, beat, w_az)
+    import torch as t
+    hb = t.from_numpy(beat).pin_memory()
+    hw = t.from_numpy(w_az.astype(np.float32)).pin_memory()
+    hq = t.from_numpy(wl.q_tx).pin_memory()
+    hr = t.from_numpy(np.ascontiguousarray(wl.q_rx)).pin_memory()
+    out = t.empty(plan.n_pixels, dtype=t.complex64).pin_memory()
+    plan.form_image_host(hb, hq, hr, out, w_az=hw)
+    assert np.array_equal(out.numpy(), dev)
+
+
+def test_invalid_arguments(torch, small):
+    import paper_2306_09784_gb300 as sar
+    wl, beat, w_az = small
+    plan = make_plan(wl)
+    b, w, qt, qr = to_dev(wl, beat, w_az)
+    lib = sar.load_library()
+    prof = plan.range_compress(b, w)
+    img = t_img = __import__("torch").zeros(plan.n_pixels, dtype=__import__("torch").complex64,
+                                            device="cuda")
+    assert lib.sar_backproject(plan.handle, prof.data_ptr(), wl.n_pulses + 1, qt.data_ptr(),
+                               qr.data_ptr(), None, img.data_ptr(), 0, None) == sar.SAR_EINVAL
+    assert lib.sar_backproject(plan.handle, None, wl.n_pulses, qt.data_ptr(), qr.data_ptr(),
+                               None, img.data_ptr(), 0, None) == sar.SAR_EINVAL
+    assert lib.sar_range_compress(plan.handle, b.data_ptr(), 0, None, prof.data_ptr(),
+                                  None) == sar.SAR_EINVAL
+    # Doppler offsets need a plan with a Doppler bound
+    fd = __import__("torch").zeros(plan.n_pixels, device="cuda")
+    assert lib.sar_backproject(plan.handle, prof.data_ptr(), wl.n_pulses, qt.data_ptr(),
+                               qr.data_ptr(), fd.data_ptr(), t_img.data_ptr(), 0,
+                               None) == sar.SAR_EINVAL
+    with pytest.raises(sar.SarError):
+        sar.Plan.from_radar(synth.Radar(n_samples=100, os=3), max_pulses=4, grid=wl.grid)
+    with pytest.raises(sar.SarError):
+        make_plan(wl, crop=(50, 40))
+
+
+def test_hbm_budget(torch, small):
+    import paper_2306_09784_gb300 as sar
+    wl, _, _ = small
+    with pytest.raises(sar.SarError) as e:
+        make_plan(wl, hbm_budget=1024)
+    assert e.value.status == sar.SAR_ENOMEM
+
+
+# ----------------------------------------------------------------------------
+# full-size configurations, sampled pixels
+# ----------------------------------------------------------------------------
+def _big(name, precision, n_sample=4096):
+    wl = synth.make_workload(name)
+    beat = synth.workload_beat(wl, device="cuda")
+    w_az = np.hanning(wl.n_pulses)
+    plan = make_plan(wl, precision=precision)
+    img = gpu_image(plan, wl, beat, w_az)
+    wins = peak_windows(wl, n_peaks=20)
+    idx = np.unique(np.concatenate([sample_pixels(len(img), n_sample)] + wins))
+    px = wl.grid.pixels()[idx]
+    ref_s = oracle_image(wl, beat, w_az, px=px)
+    pos = {int(i): k for k, i in enumerate(idx)}
+    return wl, img, idx, ref_s, wins, pos
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_config_sampled(torch, precision):
+    """Config 'full' (512^2 px, 1024 chirps x 4 Rx, jitter, clutter)."""
+    wl, img, idx, ref_s, wins, pos = _big("full", precision)
+    err = rel_l2(img[idx], ref_s)
+    print(f"full precision={precision} rel L2 = {err:.3e}")
+    assert err <= (TOL_FP32 if precision == 0 else TOL_FP16), err
+    bad = check_peaks(img[idx], ref_s, [np.array([pos[int(i)] for i in w]) for w in wins])
+    assert bad == []
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_precision_config_sampled(torch, precision):
+    """Config 'precision' (1024^2 px at 2 cm, 2048 chirps x 1024 samples x 4 Rx):
+    the benchmark workload, in the bench's launch configuration."""
+    wl, img, idx, ref_s, wins, pos = _big("precision", precision)
+    err = rel_l2(img[idx], ref_s)
+    print(f"precision-config precision={precision} rel L2 = {err:.3e}")
+    assert err <= (TOL_FP32 if precision == 0 else TOL_FP16), err
+    bad = check_peaks(img[idx], ref_s, [np.array([pos[int(i)] for i in w]) for w in wins])
+    assert bad == []
