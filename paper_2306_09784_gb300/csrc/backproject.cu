@@ -23,9 +23,20 @@
 //    (a few tens of bins).  Windows of a block of pulses are staged in shared
 //    memory as (A_k, D_k) = rot_k (S_k, S_{k+1} - S_k) pairs, so one 16-byte
 //    shared load feeds an update: v = A + f D.
+//  * Two inner loops, chosen per (tile, pulse block) by the FP64 stage:
+//    - expansion loop (the common case): Rx antennas lie millimetres from the
+//      Tx antenna, so with o = q_rx - q_tx and a = |o|^2 / 2 - (p - q_tx).o,
+//      d_rx = sqrt(d_tx^2 + 2 a) = d_tx + a / d_tx - a^2 / (2 d_tx^3) + e3,
+//      |e3| <= |o|^3 / (2 d_tx^2).  It reuses the Tx rsqrt (no MUFU per Rx)
+//      and is taken only where a1 |o|^3 / (2 (R0_tx - rho)^2) <= 2e-6 bins
+//      and the common window of the pulse's Rx channels fits;
+//    - exact loop: every distance with its own rsqrt and Newton step, and
+//      the index clamped into the window (near field, large arrays, invalid
+//      geometry).
 //  * Three-stage software pipeline per pulse block: FP64 reference ranges two
 //    blocks ahead, cp.async copies of the raw samples one block ahead, the
-//    pixel loop on the current block; one barrier per block.
+//    pixel loop on the current block; one barrier per block, which also
+//    reduces the per-block loop choice.
 #include <cuda_fp16.h>
 
 #include "sar_internal.h"
@@ -35,9 +46,13 @@ namespace {
 
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: adding it (rounding down) floors to an integer
 constexpr uint32_t kMagicBits = 0x4B400000u;
+// Truncation bound of the expansion loop, in bins of the index.
+constexpr double kExpansionTolBins = 2e-6;
 
+// Shared memory per CTA: two (A, D) table slots, one raw staging buffer and
+// three slots of per-pulse constants.
 struct Layout {
-    uint32_t table, raw, txr, rxr, pair, total;
+    uint32_t table, raw, txr, txc, rxr, rxt, pair, total;
 };
 
 __host__ __device__ inline Layout bp_layout(int Mb, int R, int L, bool fp16) {
@@ -48,11 +63,15 @@ __host__ __device__ inline Layout bp_layout(int Mb, int R, int L, bool fp16) {
     s.raw = off;
     off += (uint32_t)Mb * R * (L / 4) * 5u * (fp16 ? 4u : 8u);
     off = (off + 15u) & ~15u;
-    s.txr = off;
+    s.txr = off;  // float4 (wx, wy, R, R^2) of the Tx antenna
     off += 3u * Mb * 16u;
-    s.rxr = off;
+    s.txc = off;  // int4 (c = 2 a1 R0_tx - k_lo, k_lo, 0, 0) for the expansion loop
+    off += 3u * Mb * 16u;
+    s.rxr = off;  // float4 (wx, wy, R, R^2) of each Rx antenna (exact loop)
     off += 3u * Mb * R * 16u;
-    s.pair = off;
+    s.rxt = off;  // float4 (-o_x, -o_y, |o|^2/2 - w_tx.o, table address constant)
+    off += 3u * Mb * R * 16u;
+    s.pair = off;  // int4 (idx0 bits, table address constant, k_lo, FP16 scale bits)
     off += 3u * Mb * R * 16u;
     s.total = off;
     return s;
@@ -80,6 +99,30 @@ __device__ __forceinline__ float4 lds128(uint32_t addr) {
     return v;
 }
 
+// Single MUFU operations (flush-to-zero, no special-case fix-up sequences).
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ void sincos_approx(float x, float &s, float &c) {
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(x));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
+}
+
+// FP64 square root of x >= 0 from an FP32 reciprocal-square-root seed and one
+// Newton step on the residual x - r^2 (relative error ~1e-14, below what the
+// index and phase need).  Non-finite or negative x gives NaN.
+__device__ __forceinline__ double sqrt_fp64(double x) {
+    // outside the seed's range: tiny -> 0, huge stays huge (rejected later as
+    // beyond the maximum range), negative or NaN -> NaN
+    if (!(x >= 1e-30 && x <= 1e30))
+        return x >= 0.0 ? (x < 1e-30 ? 0.0 : x) : __longlong_as_double(0x7ff8000000000000ll);
+    const double y = (double)rsqrt_approx((float)x);
+    const double r = x * y;
+    return fma(0.5 * y, fma(-r, r, x), r);
+}
+
 // Differential range d - R for a point at offset (dx, dy) from the tile
 // reference, given w = (reference - antenna).xy, R ~ |w| and R^2 in
 // w4 = (wx, wy, R, R^2).  Exact identity: d^2 = R^2 + 2 num with
@@ -87,10 +130,11 @@ __device__ __forceinline__ float4 lds128(uint32_t addr) {
 // guess e = s y - R is refined by one Newton step on the residual
 // r = num - e (R + e / 2) = (d^2 - (R + e)^2) / 2, giving e + r y.  Relative
 // FP32 error of each term, never an absolute error of order ulp(R).
-__device__ __forceinline__ float range_delta(float4 w, float dx, float dy, float hd2) {
+// `y` returns the reciprocal distance.
+__device__ __forceinline__ float range_delta(float4 w, float dx, float dy, float hd2, float &y) {
     const float num = fmaf(w.x, dx, fmaf(w.y, dy, hd2));
     const float s = fmaf(2.0f, num, w.w);
-    const float y = rsqrtf(s);
+    y = rsqrt_approx(s);
     const float e = fmaf(s, y, -w.z);
     const float t = fmaf(0.5f, e, w.z);
     const float r = fmaf(-e, t, num);
@@ -102,8 +146,12 @@ struct Smem {
     uint32_t base_addr;
     Layout lay;
     __device__ float4 *txr(int slot, int Mb) const { return reinterpret_cast<float4 *>(base + lay.txr) + slot * Mb; }
+    __device__ int4 *txc(int slot, int Mb) const { return reinterpret_cast<int4 *>(base + lay.txc) + slot * Mb; }
     __device__ float4 *rxr(int slot, int MbR) const {
         return reinterpret_cast<float4 *>(base + lay.rxr) + slot * MbR;
+    }
+    __device__ float4 *rxt(int slot, int MbR) const {
+        return reinterpret_cast<float4 *>(base + lay.rxt) + slot * MbR;
     }
     __device__ int4 *pair(int slot, int MbR) const { return reinterpret_cast<int4 *>(base + lay.pair) + slot * MbR; }
     __device__ float4 *table(int slot, int MbRL) const {
@@ -111,14 +159,87 @@ struct Smem {
     }
 };
 
-// FP64 reference ranges of one pulse block into constant slot `cslot`, with
-// the shared-memory address constants pointing at table slot `tslot`.
-__device__ __forceinline__ void prep_block(const BpArgs &a, const Smem &sm, const TileInfo &ti, int b,
+// FP64 stage for one pulse block into constant slot `cslot`, with the
+// table address constants pointing at table slot `tslot`: the Tx records of
+// both loops and the Rx records of the expansion loop.  Tx tasks run on the
+// first warp(s), Rx tasks on the others.  Returns nonzero if one of this
+// thread's tasks rules out the expansion loop for the block: near field (an
+// antenna within 2 rho + 1 mm of the tile reference), invalid geometry, an
+// Rx offset beyond the window allowance, or the truncation bound.
+__device__ __forceinline__ int prep_block(const BpArgs &a, const Smem &sm, const TileInfo &ti, int b,
+                                          int cslot, int tslot) {
+    int exact = 0;
+    const int R = a.R, Mb = a.Mb, MbR = Mb * R;
+    const int m0 = b * Mb;
+    const int np = min(Mb, a.M - m0);
+    const int rx_base = ((Mb + 31) >> 5) << 5;
+    // largest Rx offset the common window of the expansion loop absorbs
+    const double o_allow = ((double)(a.L - 3 - 2 * kGuardBins) - 2.0 * a.fd_max - 4.0 * ti.rho * a.a1) /
+                           (2.0 * a.a1);
+    const int t = threadIdx.x;
+    if (t < rx_base) {
+        float4 *txr = sm.txr(cslot, Mb);
+        int4 *txc = sm.txc(cslot, Mb);
+        for (int p = t; p < np; p += rx_base) {
+            const double2 qt = reinterpret_cast<const double2 *>(a.q_tx)[m0 + p];
+            const double wx = ti.x - qt.x, wy = ti.y - qt.y;
+            const double r_tx = sqrt_fp64(wx * wx + wy * wy);
+            const bool ok = isfinite(r_tx) && r_tx < kMaxRange;
+            float4 t4 = make_float4(0.f, 0.f, 1.f, 1.f);
+            int4 c = make_int4(0, -(1 << 30), 0, 0);
+            if (ok) {
+                t4 = make_float4((float)wx, (float)wy, (float)r_tx, (float)(r_tx * r_tx));
+                const int k_lo =
+                    (int)floor(a.a1 * (2.0 * r_tx - 2.0 * ti.rho - o_allow) - (double)a.fd_max) - kGuardBins;
+                c = make_int4(__float_as_int((float)(2.0 * a.a1 * r_tx - (double)k_lo)), k_lo, 0, 0);
+            } else {
+                exact = 1;
+            }
+            txr[p] = t4;
+            txc[p] = c;
+        }
+    } else {
+        float4 *rxt = sm.rxt(cslot, MbR);
+        int4 *pr = sm.pair(cslot, MbR);
+        const uint32_t table_addr =
+            sm.base_addr + sm.lay.table + (uint32_t)tslot * (uint32_t)(MbR * a.L) * 16u;
+        const float rho = (float)ti.rho;
+        const float tol2 = (float)(kExpansionTolBins * 2.0 / a.a1);
+        for (int task = t - rx_base; task < np * R; task += blockDim.x - rx_base) {
+            const int p = task / R;
+            const int r = task - p * R;
+            const int m = m0 + p;
+            const double2 qt = reinterpret_cast<const double2 *>(a.q_tx)[m];
+            const double2 qr = reinterpret_cast<const double2 *>(a.q_rx)[(long long)m * R + r];
+            const double wx = ti.x - qt.x, wy = ti.y - qt.y;
+            const double ox = qr.x - qt.x, oy = qr.y - qt.y;
+            const double o2 = ox * ox + oy * oy;
+            const double cexp = 0.5 * o2 - (wx * ox + wy * oy);
+            const uint32_t addr_c = table_addr + (uint32_t)(task * a.L) * 16u - kMagicBits * 16u;
+            rxt[task] = make_float4((float)-ox, (float)-oy, (float)cexp, __uint_as_float(addr_c));
+            const float scale = a.prof_scale ? __ldg(a.prof_scale + (long long)m * R + r) : 1.0f;
+            pr[task].w = __float_as_int(scale);
+            // path criteria (FP32 is plenty; non-finite input fails them)
+            const float rt = hypotf((float)wx, (float)wy);
+            const float oa = sqrtf((float)o2);
+            const float dmin = rt - rho;
+            const bool expand = rt > 2.0f * rho + oa + 1e-3f && rt < (float)kMaxRange &&
+                                oa <= (float)o_allow && (float)o2 * oa <= tol2 * dmin * dmin;
+            exact |= expand ? 0 : 1;
+        }
+    }
+    return exact;
+}
+
+// FP64 records of the exact loop for one pulse block (blocks the expansion
+// loop cannot take): per (pulse, Rx) the Rx reference range, the window start
+// of this Rx and the reference index.  Invalid geometry is flagged and given
+// a window outside every profile.
+__device__ __forceinline__ void prep_exact(const BpArgs &a, const Smem &sm, const TileInfo &ti, int b,
                                            int cslot, int tslot) {
     const int R = a.R, Mb = a.Mb, MbR = Mb * R;
     const int m0 = b * Mb;
     const int np = min(Mb, a.M - m0);
-    float4 *txr = sm.txr(cslot, Mb);
     float4 *rxr = sm.rxr(cslot, MbR);
     int4 *pr = sm.pair(cslot, MbR);
     const uint32_t table_addr = sm.base_addr + sm.lay.table + (uint32_t)tslot * (uint32_t)(MbR * a.L) * 16u;
@@ -130,43 +251,45 @@ __device__ __forceinline__ void prep_block(const BpArgs &a, const Smem &sm, cons
         const double2 qr = reinterpret_cast<const double2 *>(a.q_rx)[(long long)m * R + r];
         const double wtx = ti.x - qt.x, wty = ti.y - qt.y;
         const double wrx = ti.x - qr.x, wry = ti.y - qr.y;
-        const double r_tx = sqrt(wtx * wtx + wty * wty);
-        const double r_rx = sqrt(wrx * wrx + wry * wry);
+        const double r_tx = sqrt_fp64(wtx * wtx + wty * wty);
+        const double r_rx = sqrt_fp64(wrx * wrx + wry * wry);
         const double d0 = r_tx + r_rx;
         const uint32_t addr_c = table_addr + (uint32_t)(task * a.L) * 16u - kMagicBits * 16u;
-        // invalid geometry contributes nothing: finite stand-in distances and a
-        // window far outside every profile (all staged samples zero)
-        const float4 dummy = make_float4(0.f, 0.f, 1.f, 1.f);
         const bool ok_tx = isfinite(r_tx) && r_tx < kMaxRange;
         const bool ok_rx = isfinite(r_rx) && r_rx < kMaxRange;
-        const float4 t4 = ok_tx ? make_float4((float)wtx, (float)wty, (float)r_tx, (float)(r_tx * r_tx)) : dummy;
-        const float4 r4 = ok_rx ? make_float4((float)wrx, (float)wry, (float)r_rx, (float)(r_rx * r_rx)) : dummy;
-        int4 q;
+        rxr[task] = ok_rx ? make_float4((float)wrx, (float)wry, (float)r_rx, (float)(r_rx * r_rx))
+                          : make_float4(0.f, 0.f, 1.f, 1.f);
+        int4 q = pr[task];
         if (ok_tx && ok_rx) {
-            const double lo = a.a1 * (d0 - 2.0 * ti.rho) - (double)a.fd_max;
-            const int k_lo = (int)floor(lo) - kGuardBins;
-            const float idx0 = (float)(a.a1 * d0 - (double)k_lo);
-            q = make_int4(__float_as_int(idx0), (int)addr_c, k_lo, 1);
+            const int k_lo = (int)floor(a.a1 * (d0 - 2.0 * ti.rho) - (double)a.fd_max) - kGuardBins;
+            q.x = __float_as_int((float)(a.a1 * d0 - (double)k_lo));
+            q.z = k_lo;
         } else {
-            q = make_int4(__float_as_int((float)kGuardBins), (int)addr_c, -(1 << 30), 0);
+            q.x = __float_as_int((float)kGuardBins);
+            q.z = -(1 << 30);
             atomicOr(a.err, 1);
         }
-        if (r == 0) txr[p] = t4;
-        rxr[task] = r4;
+        q.y = (int)addr_c;
         pr[task] = q;
     }
+}
+
+// Window start of (pulse p, Rx r): per Rx in the exact loop, per pulse in
+// the expansion loop.
+__device__ __forceinline__ int window_start(const Smem &sm, int cslot, int Mb, int MbR, int w, int p,
+                                            bool exact) {
+    return exact ? sm.pair(cslot, MbR)[w].z : sm.txc(cslot, Mb)[p].y;
 }
 
 // Issue cp.async copies of the raw profile samples of one pulse block.  Item
 // = (window w, group q of 4 entries) = samples k_lo + 4q .. k_lo + 4q + 4.
 // Samples outside [crop_lo, crop_hi] are zero-filled.
 template <bool FP16>
-__device__ __forceinline__ void stage_block(const BpArgs &a, const Smem &sm, int b, int cslot) {
+__device__ __forceinline__ void stage_block(const BpArgs &a, const Smem &sm, int b, int cslot, bool exact) {
     constexpr int SB = FP16 ? 4 : 8;
     const int R = a.R, Mb = a.Mb, MbR = Mb * R;
     const int np = min(Mb, a.M - b * Mb);
     const int nq = a.L >> 2;
-    const int4 *pr = sm.pair(cslot, MbR);
     const unsigned char *prof = reinterpret_cast<const unsigned char *>(a.prof);
     const uint32_t raw = sm.base_addr + sm.lay.raw;
     const int n_items = np * R * nq;
@@ -177,7 +300,7 @@ __device__ __forceinline__ void stage_block(const BpArgs &a, const Smem &sm, int
         const int r = w - p * R;
         const long long row = (long long)(b * Mb + p) * R + r;
         const unsigned char *rowp = prof + row * a.n_bins * SB;
-        const int k0 = pr[w].z + 4 * q;
+        const int k0 = window_start(sm, cslot, Mb, MbR, w, p, exact) + 4 * q;
         const uint32_t dst = raw + (uint32_t)it * 5u * SB;
 #pragma unroll
         for (int e = 0; e < 5; ++e) {
@@ -191,7 +314,8 @@ __device__ __forceinline__ void stage_block(const BpArgs &a, const Smem &sm, int
 
 // Convert this thread's staged raw samples into (A, D) table entries.
 template <bool FP16>
-__device__ __forceinline__ void convert_block(const BpArgs &a, const Smem &sm, int b, int cslot, int tslot) {
+__device__ __forceinline__ void convert_block(const BpArgs &a, const Smem &sm, int b, int cslot, int tslot,
+                                              bool exact) {
     constexpr int SB = FP16 ? 4 : 8;
     const int R = a.R, Mb = a.Mb, MbR = Mb * R;
     const int np = min(Mb, a.M - b * Mb);
@@ -203,12 +327,11 @@ __device__ __forceinline__ void convert_block(const BpArgs &a, const Smem &sm, i
     for (int it = threadIdx.x; it < n_items; it += blockDim.x) {
         const int w = it / nq;
         const int q = it - w * nq;
-        const int k0 = pr[w].z + 4 * q;
+        const int p = w / R;
+        const int k0 = window_start(sm, cslot, Mb, MbR, w, p, exact) + 4 * q;
         float2 s[5];
         if (FP16) {
-            const int p = w / R;
-            const int r = w - p * R;
-            const float sc = __ldg(a.prof_scale + (long long)(b * Mb + p) * R + r);
+            const float sc = __int_as_float(pr[w].w);
             const __half2 *h = reinterpret_cast<const __half2 *>(raw + (size_t)it * 5 * SB);
 #pragma unroll
             for (int e = 0; e < 5; ++e) {
@@ -232,11 +355,80 @@ __device__ __forceinline__ void convert_block(const BpArgs &a, const Smem &sm, i
     }
 }
 
+// One update: interpolate entry (A, D) at fractional index f and accumulate
+// (A + f D) exp(sign j 2 pi beta f).
+__device__ __forceinline__ void accumulate(float idx, uint32_t ac, float k2pb, float &acc_re, float &acc_im) {
+    const float tm = __fadd_rd(idx, kMagic);
+    const float f = idx - (tm - kMagic);
+    const float4 e = lds128((__float_as_uint(tm) << 4) + ac);
+    const float vre = fmaf(f, e.z, e.x);
+    const float vim = fmaf(f, e.w, e.y);
+    float sn, cs;
+    sincos_approx(f * k2pb, sn, cs);
+    acc_re = fmaf(vre, cs, acc_re);
+    acc_im = fmaf(vre, sn, acc_im);
+    acc_re = fmaf(-vim, sn, acc_re);
+    acc_im = fmaf(vim, cs, acc_im);
+}
+
+// Expansion loop over one pulse block (far field, small Rx offsets).
 template <int RG, bool FD>
-__device__ __forceinline__ void compute_block(const BpArgs &a, const Smem &sm, int b, int cslot,
-                                              const float (&dx)[kPxPerThread], const float (&dy)[kPxPerThread],
-                                              const float (&hd2)[kPxPerThread], const float (&fdm)[kPxPerThread],
-                                              float (&acc_re)[kPxPerThread], float (&acc_im)[kPxPerThread]) {
+__device__ __forceinline__ void compute_block_expand(const BpArgs &a, const Smem &sm, int b, int cslot,
+                                                     const float (&dx)[kPxPerThread],
+                                                     const float (&dy)[kPxPerThread],
+                                                     const float (&hd2)[kPxPerThread],
+                                                     const float (&fdi)[kPxPerThread],
+                                                     float (&acc_re)[kPxPerThread],
+                                                     float (&acc_im)[kPxPerThread]) {
+    const int R = a.R, Mb = a.Mb, MbR = Mb * R;
+    const int np = min(Mb, a.M - b * Mb);
+    const float4 *txr = sm.txr(cslot, Mb);
+    const int4 *txc = sm.txc(cslot, Mb);
+    const float4 *rxt = sm.rxt(cslot, MbR);
+    const float a1 = a.a1f, two_a1 = 2.0f * a.a1f, half_a1 = 0.5f * a.a1f;
+    const float k2pb = a.two_pi_beta;
+    for (int p = 0; p < np; ++p) {
+        const float4 t4 = txr[p];
+        const float cidx = __int_as_float(txc[p].x);
+        float u[kPxPerThread], ay[kPxPerThread], kk[kPxPerThread];
+#pragma unroll
+        for (int j = 0; j < kPxPerThread; ++j) {
+            float y;
+            const float dt = range_delta(t4, dx[j], dy[j], hd2[j], y);
+            // index of the Tx part (twice the Tx range) and the expansion
+            // coefficients a1/d and a1/(2 d^3)
+            u[j] = fmaf(two_a1, dt, FD ? cidx + fdi[j] : cidx);
+            ay[j] = a1 * y;
+            kk[j] = (half_a1 * y) * (y * y);
+        }
+        for (int r0 = 0; r0 < R; r0 += RG) {
+#pragma unroll
+            for (int rr = 0; rr < RG; ++rr) {
+                const float4 o4 = rxt[p * R + r0 + rr];
+                const uint32_t ac = __float_as_uint(o4.w);
+#pragma unroll
+                for (int j = 0; j < kPxPerThread; ++j) {
+                    // a = |o|^2/2 - (p - q_tx).o;  a1 (d_rx - d_tx) = a (a1/d - a a1/(2 d^3))
+                    const float av = fmaf(o4.x, dx[j], fmaf(o4.y, dy[j], o4.z));
+                    const float m1 = fmaf(-av, kk[j], ay[j]);
+                    const float idx = fmaf(av, m1, u[j]);
+                    accumulate(idx, ac, k2pb, acc_re[j], acc_im[j]);
+                }
+            }
+        }
+    }
+}
+
+// Exact loop over one pulse block: every distance from its own rsqrt and
+// Newton step, the index clamped into the staged window.
+template <int RG, bool FD>
+__device__ __forceinline__ void compute_block_exact(const BpArgs &a, const Smem &sm, int b, int cslot,
+                                                    const float (&dx)[kPxPerThread],
+                                                    const float (&dy)[kPxPerThread],
+                                                    const float (&hd2)[kPxPerThread],
+                                                    const float (&fdi)[kPxPerThread],
+                                                    float (&acc_re)[kPxPerThread],
+                                                    float (&acc_im)[kPxPerThread]) {
     const int R = a.R, Mb = a.Mb, MbR = Mb * R;
     const int np = min(Mb, a.M - b * Mb);
     const float4 *txr = sm.txr(cslot, Mb);
@@ -250,8 +442,8 @@ __device__ __forceinline__ void compute_block(const BpArgs &a, const Smem &sm, i
         float dt[kPxPerThread];
 #pragma unroll
         for (int j = 0; j < kPxPerThread; ++j) {
-            dt[j] = range_delta(t4, dx[j], dy[j], hd2[j]);
-            if (FD) dt[j] += fdm[j];
+            float y;
+            dt[j] = range_delta(t4, dx[j], dy[j], hd2[j], y);
         }
         for (int r0 = 0; r0 < R; r0 += RG) {
 #pragma unroll
@@ -263,20 +455,12 @@ __device__ __forceinline__ void compute_block(const BpArgs &a, const Smem &sm, i
                 const uint32_t ac = (uint32_t)pq.y;
 #pragma unroll
                 for (int j = 0; j < kPxPerThread; ++j) {
-                    const float drx = range_delta(q4, dx[j], dy[j], hd2[j]);
+                    float y;
+                    const float drx = range_delta(q4, dx[j], dy[j], hd2[j], y);
                     float idx = fmaf(a1, dt[j] + drx, idx0);
+                    if (FD) idx += fdi[j];
                     idx = fminf(fmaxf(idx, 0.0f), lmax);
-                    const float tm = __fadd_rd(idx, kMagic);
-                    const float f = idx - (tm - kMagic);
-                    const float4 e = lds128((__float_as_uint(tm) << 4) + ac);
-                    const float vre = fmaf(f, e.z, e.x);
-                    const float vim = fmaf(f, e.w, e.y);
-                    float sn, cs;
-                    __sincosf(f * k2pb, &sn, &cs);
-                    acc_re[j] = fmaf(vre, cs, acc_re[j]);
-                    acc_im[j] = fmaf(vre, sn, acc_im[j]);
-                    acc_re[j] = fmaf(-vim, sn, acc_re[j]);
-                    acc_im[j] = fmaf(vim, cs, acc_im[j]);
+                    accumulate(idx, ac, k2pb, acc_re[j], acc_im[j]);
                 }
             }
         }
@@ -303,8 +487,7 @@ __global__ void __launch_bounds__(kBpThreads, 2) backproject_kernel(BpArgs a) {
         const int b1 = (int)min((long long)PB, (long long)b0 + (u1 - u));
         const TileInfo ti = a.tiles[tile];
 
-        float dx[kPxPerThread], dy[kPxPerThread], hd2[kPxPerThread], fdm[kPxPerThread];
-        float fdc[kPxPerThread];
+        float dx[kPxPerThread], dy[kPxPerThread], hd2[kPxPerThread], fdi[kPxPerThread];
         int oi[kPxPerThread];
         float acc_re[kPxPerThread], acc_im[kPxPerThread];
 #pragma unroll
@@ -315,36 +498,47 @@ __global__ void __launch_bounds__(kBpThreads, 2) backproject_kernel(BpArgs a) {
             dx[j] = d.x;
             dy[j] = d.y;
             hd2[j] = 0.5f * fmaf(d.x, d.x, d.y * d.y);
-            fdm[j] = 0.f;
-            fdc[j] = 0.f;
-            if (FD && oi[j] >= 0) {
-                const float fd = fminf(fmaxf(a.fdopp[oi[j]], -a.fd_max), a.fd_max);
-                fdm[j] = fd / a.a1f;  // in metres of d, added to the Tx delta
-                fdc[j] = fd;
-            }
+            fdi[j] = 0.f;
+            if (FD && oi[j] >= 0) fdi[j] = fminf(fmaxf(a.fdopp[oi[j]], -a.fd_max), a.fd_max);
             acc_re[j] = 0.f;
             acc_im[j] = 0.f;
         }
 
-        // pipeline prologue
-        prep_block(a, sm, ti, b0, 0, 0);
-        if (b0 + 1 < b1) prep_block(a, sm, ti, b0 + 1, 1, 1);
-        __syncthreads();
-        stage_block<FP16>(a, sm, b0, 0);
+        // pipeline prologue; the loop choices (exact or expansion) of blocks
+        // b, b+1, b+2 are block-uniform (reduced by the barriers)
+        int fl = prep_block(a, sm, ti, b0, 0, 0);
+        if (b0 + 1 < b1) fl |= prep_block(a, sm, ti, b0 + 1, 1, 1) << 1;
+        int ex_cur = __syncthreads_or(fl & 1);
+        int ex_next = __syncthreads_or(fl & 2) ? 1 : 0;
+        if (ex_cur) {
+            prep_exact(a, sm, ti, b0, 0, 0);
+            __syncthreads();
+        }
+        stage_block<FP16>(a, sm, b0, 0, ex_cur);
         cp_async_commit();
         cp_async_wait_all();
-        convert_block<FP16>(a, sm, b0, 0, 0);
+        convert_block<FP16>(a, sm, b0, 0, 0, ex_cur);
         __syncthreads();
 
         for (int b = b0; b < b1; ++b) {
             const int k = b - b0;
-            if (b + 2 < b1) prep_block(a, sm, ti, b + 2, (k + 2) % 3, (k + 2) & 1);
-            if (b + 1 < b1) stage_block<FP16>(a, sm, b + 1, (k + 1) % 3);
+            int ex_new = 0;
+            if (b + 2 < b1) ex_new = prep_block(a, sm, ti, b + 2, (k + 2) % 3, (k + 2) & 1);
+            if (b + 1 < b1 && ex_next) {  // block-uniform
+                prep_exact(a, sm, ti, b + 1, (k + 1) % 3, (k + 1) & 1);
+                __syncthreads();
+            }
+            if (b + 1 < b1) stage_block<FP16>(a, sm, b + 1, (k + 1) % 3, ex_next);
             cp_async_commit();
-            compute_block<RG, FD>(a, sm, b, k % 3, dx, dy, hd2, fdm, acc_re, acc_im);
+            if (ex_cur)
+                compute_block_exact<RG, FD>(a, sm, b, k % 3, dx, dy, hd2, fdi, acc_re, acc_im);
+            else
+                compute_block_expand<RG, FD>(a, sm, b, k % 3, dx, dy, hd2, fdi, acc_re, acc_im);
             cp_async_wait_all();
-            if (b + 1 < b1) convert_block<FP16>(a, sm, b + 1, (k + 1) % 3, (k + 1) & 1);
-            __syncthreads();
+            if (b + 1 < b1) convert_block<FP16>(a, sm, b + 1, (k + 1) % 3, (k + 1) & 1, ex_next);
+            ex_new = __syncthreads_or(ex_new);
+            ex_cur = ex_next;
+            ex_next = ex_new;
         }
 
         if (FD) {
@@ -352,7 +546,7 @@ __global__ void __launch_bounds__(kBpThreads, 2) backproject_kernel(BpArgs a) {
             // exp(sign j 2 pi beta f_doppler) of the per-index phase
 #pragma unroll
             for (int j = 0; j < kPxPerThread; ++j) {
-                float cyc = a.beta * fdc[j];
+                float cyc = a.beta * fdi[j];
                 cyc -= rintf(cyc);
                 float sn, cs;
                 sincospif(-2.0f * a.sign * cyc, &sn, &cs);
@@ -421,10 +615,10 @@ void *kernel_ptr() {
 }
 
 void *select_kernel(int rg, bool fp16, bool fd) {
-#define SAR_SEL(RGV)                                                              \
-    if (rg == RGV) {                                                              \
-        if (fp16) return fd ? kernel_ptr<RGV, true, true>() : kernel_ptr<RGV, true, false>();   \
-        return fd ? kernel_ptr<RGV, false, true>() : kernel_ptr<RGV, false, false>();           \
+#define SAR_SEL(RGV)                                                                          \
+    if (rg == RGV) {                                                                          \
+        if (fp16) return fd ? kernel_ptr<RGV, true, true>() : kernel_ptr<RGV, true, false>(); \
+        return fd ? kernel_ptr<RGV, false, true>() : kernel_ptr<RGV, false, false>();         \
     }
     SAR_SEL(1)
     SAR_SEL(2)
