@@ -59,6 +59,10 @@ __host__ __device__ constexpr int bitrev(int i, int bits) {
     return r;
 }
 
+// Shared-memory index with one spare element after every 16: the
+// stride-16 stores of the first passes then spread over all banks.
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
 template <int RAD>
 __host__ __device__ constexpr int ilog2(int) {
     return RAD == 2 ? 1 : RAD == 4 ? 2 : RAD == 8 ? 3 : 4;
@@ -120,7 +124,7 @@ __device__ __forceinline__ void stockham_pass(float2 *X, int n, int log2n, int N
                 }
                 v[g * RAD + r] = x;
             } else {
-                v[g * RAD + r] = X[idx];
+                v[g * RAD + r] = X[pad16(idx)];
             }
         }
     }
@@ -140,13 +144,15 @@ __device__ __forceinline__ void stockham_pass(float2 *X, int n, int log2n, int N
         dft_reg<RAD, SGN>(v + g * RAD);
         const int base = (j - k) * RAD + k;
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) X[base + r * Ns] = v[g * RAD + r];
+        for (int r = 0; r < RAD; ++r) X[pad16(base + r * Ns)] = v[g * RAD + r];
     }
     __syncthreads();
 }
 
-template <int SGN, int MODE>
-__global__ void __launch_bounds__(1024) range_compress_kernel(RcArgs a) {
+// BIG: N_fft of 8192 or 16384 (512 or 1024 threads per row); otherwise at
+// most 256 threads per CTA and registers to spare for the 16 values in flight.
+template <int SGN, int MODE, bool BIG>
+__global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 3) range_compress_kernel(RcArgs a) {
     extern __shared__ float2 smem_rc[];
     __shared__ int row_max[64];  // rows per CTA <= 4096 / 64
     const int n = a.n_fft;
@@ -156,7 +162,7 @@ __global__ void __launch_bounds__(1024) range_compress_kernel(RcArgs a) {
     const int tid = threadIdx.x - lrow * T;
     const long long row = (long long)blockIdx.x * rows_per_cta + lrow;
     const bool active = row < a.rows;
-    float2 *X = smem_rc + (size_t)lrow * n;
+    float2 *X = smem_rc + (size_t)lrow * (n + n / 16);
     const float2 *beat_row = a.beat + (active ? row : 0) * (long long)a.N;
 
     if (MODE == kRcProfileF16 && threadIdx.x < 64) row_max[threadIdx.x] = 0;
@@ -179,7 +185,7 @@ __global__ void __launch_bounds__(1024) range_compress_kernel(RcArgs a) {
     if (MODE == kRcSpectrum) {
         if (!active) return;
         float2 *out = reinterpret_cast<float2 *>(a.out) + row * (long long)n;
-        for (int k = tid; k < n; k += T) out[k] = X[k];
+        for (int k = tid; k < n; k += T) out[k] = X[pad16(k)];
         return;
     }
 
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(1024) range_compress_kernel(RcArgs a) {
         if (!active) return;
         float2 *out = reinterpret_cast<float2 *>(a.out) + row * (long long)a.n_bins;
         for (int i = tid; i < a.n_bins; i += T) {
-            const float2 v = cmul(X[a.crop_lo + i], __ldg(a.rot + i));
+            const float2 v = cmul(X[pad16(a.crop_lo + i)], __ldg(a.rot + i));
             out[i] = make_float2(g * v.x, g * v.y);
         }
         return;
@@ -198,7 +204,7 @@ __global__ void __launch_bounds__(1024) range_compress_kernel(RcArgs a) {
     float mx = 0.f;
     if (active) {
         for (int i = tid; i < a.n_bins; i += T) {
-            const float2 v = cmul(X[a.crop_lo + i], __ldg(a.rot + i));
+            const float2 v = cmul(X[pad16(a.crop_lo + i)], __ldg(a.rot + i));
             mx = fmaxf(mx, fmaxf(fabsf(g * v.x), fabsf(g * v.y)));
         }
     }
@@ -211,7 +217,7 @@ __global__ void __launch_bounds__(1024) range_compress_kernel(RcArgs a) {
     if (tid == 0) a.scales[row] = scale;
     __half2 *out = reinterpret_cast<__half2 *>(a.out) + row * (long long)a.n_bins;
     for (int i = tid; i < a.n_bins; i += T) {
-        const float2 v = cmul(X[a.crop_lo + i], __ldg(a.rot + i));
+        const float2 v = cmul(X[pad16(a.crop_lo + i)], __ldg(a.rot + i));
         out[i] = __floats2half2_rn(g * v.x * inv, g * v.y * inv);
     }
 }
@@ -222,8 +228,8 @@ cudaError_t launch_rc(const RcArgs &a, cudaStream_t s) {
     const int T = n / 16;
     const int rows_per_cta = n >= 4096 ? 1 : 4096 / n;
     const int threads = T * rows_per_cta;
-    const size_t smem = (size_t)rows_per_cta * n * sizeof(float2);
-    auto kern = range_compress_kernel<SGN, MODE>;
+    const size_t smem = (size_t)rows_per_cta * (n + n / 16) * sizeof(float2);
+    auto kern = n > 4096 ? range_compress_kernel<SGN, MODE, true> : range_compress_kernel<SGN, MODE, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long blocks = (a.rows + rows_per_cta - 1) / rows_per_cta;
