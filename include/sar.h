@@ -37,7 +37,8 @@ enum sar_status {
     SAR_ETIMEOUT = 4,  /* a bounded wait ran out */
     SAR_ECUDA = 5,     /* a CUDA runtime call failed */
     SAR_EBOUNDS = 6,   /* a kernel saw invalid geometry (non-finite or out of range) */
-    SAR_ENOTFOUND = 7  /* unknown ticket */
+    SAR_ENOTFOUND = 7, /* unknown ticket */
+    SAR_ESCRATCH = 8   /* sar_backproject_noalloc: the call needs more than its static scratch */
 };
 
 enum sar_window { SAR_WINDOW_RECT = 0, SAR_WINDOW_HANN = 1, SAR_WINDOW_KAISER = 2 };
@@ -191,6 +192,36 @@ int sar_backproject(sar_plan *plan, const void *prof_dev, int32_t M,
                     const double *q_tx_dev, const double *q_rx_dev,
                     const float *fdopp_idx_dev, void *image_dev,
                     int32_t accumulate, void *stream);
+
+/*
+ * sar_backproject without any device allocation on the library's side, for
+ * callers that cannot allocate device memory when they image a frame: an
+ * embedded or safety-certified automotive process that allocates only at
+ * start-up, or a caller whose device memory is reserved up front by another
+ * allocator.  (The paper has no counterpart; this is an interface matter.)
+ *
+ * Same arguments, result and errors as sar_backproject.  The plan's
+ * read-only tables are still used; only the scratch for tiles that several
+ * CTAs share (partial sums, up to 8 KB per CTA and tile) comes from one
+ * static 16 MiB device array in the library, which every GPU that loads the
+ * library holds until the process exits.
+ *  - A call whose work would need more than those 16 MiB returns
+ *    SAR_ESCRATCH and enqueues nothing (a 1024 x 1024 image needs ~12.5 MB on
+ *    a 152-SM GPU; about 1300 tiles of 32 x 32 points fit).
+ *  - The first call on a device looks up the array's device address (a
+ *    runtime symbol lookup, no allocation); make that first call before any
+ *    stream capture.
+ *  - Every call on a device shares the one array and finds the previous
+ *    call's contents there; nothing in it needs to start at zero (each slot
+ *    read is written earlier in the same call).  Calls whose work overlaps on
+ *    the GPU (several streams, several host threads) race on it: serialise
+ *    them.
+ *  - The call itself makes no cudaMalloc, cudaFree or other allocating call.
+ */
+int sar_backproject_noalloc(sar_plan *plan, const void *prof_dev, int32_t M,
+                            const double *q_tx_dev, const double *q_rx_dev,
+                            const float *fdopp_idx_dev, void *image_dev,
+                            int32_t accumulate, void *stream);
 
 /*
  * Whole frame from host memory: copy beat, w_sar and trajectory to the

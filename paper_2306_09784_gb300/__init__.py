@@ -16,7 +16,8 @@ from typing import Optional
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libsar.so")
 
-SAR_OK, SAR_EINVAL, SAR_ENOMEM, SAR_EAGAIN, SAR_ETIMEOUT, SAR_ECUDA, SAR_EBOUNDS, SAR_ENOTFOUND = range(8)
+(SAR_OK, SAR_EINVAL, SAR_ENOMEM, SAR_EAGAIN, SAR_ETIMEOUT, SAR_ECUDA, SAR_EBOUNDS, SAR_ENOTFOUND,
+ SAR_ESCRATCH) = range(9)
 WINDOW_RECT, WINDOW_HANN, WINDOW_KAISER = 0, 1, 2
 PREC_FP32, PREC_FP16 = 0, 1
 
@@ -24,7 +25,7 @@ PREC_FP32, PREC_FP16 = 0, 1
 EXPORTS = (
     "sar_plan_create", "sar_plan_destroy", "sar_plan_get_info", "sar_profile_bytes",
     "sar_range_compress", "sar_range_spectrum", "sar_backproject", "sar_form_image_host",
-    "sar_plan_check_errors", "sar_status_string", "sar_version",
+    "sar_plan_check_errors", "sar_status_string", "sar_version", "sar_backproject_noalloc",
 )
 
 
@@ -86,6 +87,7 @@ def load_library(path: str = LIB_PATH):
     lib.sar_range_compress.argtypes = [vp, vp, i32, vp, vp, vp]
     lib.sar_range_spectrum.argtypes = [vp, vp, i32, vp, vp]
     lib.sar_backproject.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32, vp]
+    lib.sar_backproject_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32, vp]
     lib.sar_form_image_host.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
     lib.sar_plan_check_errors.argtypes = [vp]
     lib.sar_status_string.argtypes = [ctypes.c_int]

@@ -496,6 +496,68 @@ int bp_launch(sar_plan *pl, const void *prof, int M, const double *q_tx, const d
 
 }  // namespace
 
+namespace sar {
+
+int plan_device(const sar_plan *pl) { return pl->device; }
+
+// The launch of sar_backproject with the split-tile partial sums in
+// `scratch` (scratch_bytes long) instead of the plan's own buffer.  Returns
+// SAR_ESCRATCH when this call's decomposition needs more than scratch_bytes.
+int backproject_with_scratch(sar_plan *pl, const void *prof, int M, const double *q_tx, const double *q_rx,
+                             const float *fd, void *image, int accumulate, float2 *scratch, size_t scratch_bytes,
+                             cudaStream_t s) {
+    if (!pl || M < 1 || M > pl->p.max_pulses) return SAR_EINVAL;
+    if (fd && !(pl->fd_max > 0)) return SAR_EINVAL;
+    BpArgs a{};
+    const size_t rows = (size_t)M * pl->p.n_rx;
+    if (pl->fp16) {
+        a.prof_scale = (const float *)prof;
+        a.prof = (const unsigned char *)prof + ((rows * 4 + 255) & ~size_t(255));
+    } else {
+        a.prof = prof;
+        a.prof_scale = nullptr;
+    }
+    a.q_tx = q_tx;
+    a.q_rx = q_rx;
+    a.fdopp = fd;
+    a.image = (float2 *)image;
+    a.partial = scratch;
+    a.err = pl->d_err;
+    a.pix = pl->d_pix;
+    a.out_idx = pl->d_out;
+    a.tiles = pl->d_tiles;
+    a.M = M;
+    a.R = pl->p.n_rx;
+    a.n_tiles = pl->n_tiles;
+    a.Mb = pl->Mb;
+    a.L = pl->L;
+    a.blocks_per_tile = (M + pl->Mb - 1) / pl->Mb;
+    a.units = (long long)pl->n_tiles * a.blocks_per_tile;
+    a.G = (int)std::min<long long>(pl->G, a.units);
+    const long long per = (a.units + a.G - 1) / a.G;
+    a.seg_max = (int)((per - 1) / a.blocks_per_tile) + 2;
+    a.n_bins = pl->n_bins;
+    a.crop_lo = pl->crop_lo;
+    a.crop_hi = pl->crop_hi;
+    a.accumulate = accumulate ? 1 : 0;
+    a.a1 = pl->a1;
+    a.a1f = (float)pl->a1;
+    a.two_pi_beta = (float)(pl->sign * 2.0 * kPi * pl->beta);
+    a.beta = (float)pl->beta;
+    a.sign = (float)pl->sign;
+    const double cb = -pl->sign * 2.0 * kPi * (pl->beta - std::floor(pl->beta));
+    a.cb = make_float2((float)std::cos(cb), (float)std::sin(cb));
+    a.fd_max = pl->fd_max;
+    const size_t need = (size_t)a.G * (size_t)a.seg_max * kTilePx * sizeof(float2);
+    if (need > scratch_bytes) return SAR_ESCRATCH;
+    BpLaunch l{pl->rg, pl->fp16, pl->bp_smem};
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return SAR_ECUDA;
+    return launch_backproject(a, l, s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
+}
+
+}  // namespace sar
+
 extern "C" {
 
 int sar_version(void) { return 100; }
@@ -510,6 +572,7 @@ const char *sar_status_string(int st) {
         case SAR_ECUDA: return "CUDA error";
         case SAR_EBOUNDS: return "invalid geometry skipped";
         case SAR_ENOTFOUND: return "unknown ticket";
+        case SAR_ESCRATCH: return "work needs more than the 16 MiB static scratch of sar_backproject_noalloc";
         default: return "unknown status";
     }
 }

@@ -88,4 +88,10 @@ cudaError_t bp_prepare(bool fp16, int rg, size_t smem);  // sets function attrib
 int bp_occupancy(bool fp16, int rg, size_t smem, int *ctas_per_sm);
 cudaError_t launch_backproject(const BpArgs &a, const BpLaunch &l, cudaStream_t s);
 
+// Used by sar_backproject_noalloc (noalloc.cu).
+int plan_device(const sar_plan *pl);
+int backproject_with_scratch(sar_plan *pl, const void *prof, int M, const double *q_tx, const double *q_rx,
+                             const float *fd, void *image, int accumulate, float2 *scratch, size_t scratch_bytes,
+                             cudaStream_t s);
+
 }  // namespace sar
