@@ -251,6 +251,76 @@ def rc_roofline(plan, M, R, N, rc_ms):
             "algorithmic_bytes": bytes_, "peak_basis": f"{basis} copy bandwidth"}
 
 
+def bench_batched(dev, stream, reps=5, n_req=64, seed=5):
+    """Batched form: 64 uneven requests (128-1024 pulses, 128^2-768^2 px, 1-4 Rx,
+    FP16 profiles).  Frames/s of per-request plain launches (range compression
+    + backprojection + fix-up per request) against the same range compressions
+    plus ONE persistent batched backprojection, captured in a CUDA graph."""
+    import torch
+    import paper_2306_09784_gb300 as sar
+    wls = synth.make_batched_requests(n_req, seed=seed)
+    reqs = []
+    for wl in wls:
+        beat = torch.from_numpy(synth.workload_beat(wl, device=str(dev))).to(dev)
+        w = torch.from_numpy(synth.azimuth_weights(wl.n_pulses).astype(np.float32)).to(dev)
+        plan = sar.Plan.from_radar(wl.radar, max_pulses=wl.n_pulses, grid=wl.grid,
+                                   precision=sar.PREC_FP16, crop=wl.crop)
+        reqs.append(dict(wl=wl, beat=beat, w=w, plan=plan,
+                         qt=torch.from_numpy(wl.q_tx).to(dev),
+                         qr=torch.from_numpy(np.ascontiguousarray(wl.q_rx)).to(dev),
+                         prof=plan.empty_profiles(wl.n_pulses, dev),
+                         img_plain=torch.zeros(plan.n_pixels, dtype=torch.complex64, device=dev),
+                         img_batch=torch.zeros(plan.n_pixels, dtype=torch.complex64, device=dev)))
+    upd = sum(r["wl"].grid.nx * r["wl"].grid.ny * r["wl"].n_pulses * r["wl"].radar.n_rx for r in reqs)
+
+    def plain():
+        for r in reqs:
+            r["plan"].range_compress(r["beat"], r["w"], out=r["prof"], stream=stream)
+            r["plan"].backproject(r["prof"], r["wl"].n_pulses, r["qt"], r["qr"], image=r["img_plain"],
+                                  stream=stream)
+
+    batch = sar.Batch(len(reqs))
+    for r in reqs:
+        batch.add(r["plan"], r["prof"], r["wl"].n_pulses, r["qt"], r["qr"], r["img_batch"])
+    with torch.cuda.stream(stream):
+        batch.commit(stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        for r in reqs:
+            r["plan"].range_compress(r["beat"], r["w"], out=r["prof"], stream=stream)
+        batch.launch(stream)
+
+    def timed(fn):
+        # everything (including graph replays, which run on the current
+        # stream) on `stream`, bracketed by events on that stream
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    t_plain = timed(plain)
+    t_batch = timed(graph.replay)
+    errs = [float((r["img_batch"] - r["img_plain"]).abs().norm() / r["img_plain"].abs().norm())
+            for r in reqs]
+    _, units, ctas = batch.info()
+    return {"requests": len(reqs), "updates": upd,
+            "plain_frames_per_s": len(reqs) / t_plain, "batched_frames_per_s": len(reqs) / t_batch,
+            "plain_ms": t_plain * 1e3, "batched_ms": t_batch * 1e3,
+            "speedup": t_plain / t_batch, "batched_gupdates_per_s": upd / t_batch / 1e9,
+            "max_rel_l2_batched_vs_plain": max(errs), "work_units": units, "ctas": ctas,
+            "config": "64 requests, 128-1024 chirps x 512 samples, 128^2-768^2 px at 2.5 cm, "
+                      "1-4 Rx, FP16 profiles; batched = same range compressions + one persistent "
+                      "backprojection launch, replayed as one CUDA graph"}
+
+
 def run_ours(args):
     import torch
     import paper_2306_09784_gb300 as sar
@@ -374,6 +444,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3},
         "gpu_launches": 3 * args.steps,
     }
+    if rank == 0 and not args.no_batched:
+        line["batched"] = bench_batched(dev, torch.cuda.Stream(dev))
     if rank == 0 and not args.no_cpu_baseline:
         cb, vals, idx = cpu_baseline(wl, beat_np, w_az)
         torch.cuda.synchronize(dev)
@@ -398,6 +470,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp16", "fp32"], default="fp16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -224,6 +224,41 @@ int sar_backproject_noalloc(sar_plan *plan, const void *prof_dev, int32_t M,
                             int32_t accumulate, void *stream);
 
 /*
+ * Batched backprojection (Alg. 2 for several requests in one launch).
+ * Requests of uneven sizes -- each with its own plan (radar parameters,
+ * reconstruction points, FP32 or FP16 profiles), profiles, trajectory and
+ * image -- are packed as (request, pixel tile, pulse block) work units and
+ * split evenly over one persistent grid; tiles shared by two CTAs are summed
+ * by a fix-up kernel.  Each request's image equals sar_backproject's up to
+ * FP32 summation order.
+ *
+ * Use: sar_batch_clear, sar_batch_add per request, sar_batch_commit (uploads
+ * the request table on `stream`), then sar_batch_launch (two kernels on
+ * `stream`, reading only device memory: it can be captured in a CUDA graph
+ * and replayed while the table and the request buffers stay unchanged).
+ * All plans of a batch must be on the batch's device; the batch owns its
+ * request table (pinned host + device) and 16 KB of scratch per CTA.
+ * Requests of one batch must not write the same image.
+ */
+typedef struct sar_batch sar_batch;
+
+/* Create a batch for up to max_jobs requests on the current device. */
+int sar_batch_create(int32_t max_jobs, sar_batch **out);
+void sar_batch_destroy(sar_batch *batch);
+/* Forget all requests (waits for a pending table upload). */
+int sar_batch_clear(sar_batch *batch);
+/* Append one request: arguments as sar_backproject (no Doppler offsets). */
+int sar_batch_add(sar_batch *batch, sar_plan *plan, const void *prof_dev, int32_t M,
+                  const double *q_tx_dev, const double *q_rx_dev, void *image_dev,
+                  int32_t accumulate);
+/* Upload the request table asynchronously on `stream`. */
+int sar_batch_commit(sar_batch *batch, void *stream);
+/* Launch the persistent backprojection and its fix-up over all requests. */
+int sar_batch_launch(sar_batch *batch, void *stream);
+/* Requests, work units and CTAs of the committed batch (any pointer may be NULL). */
+int sar_batch_get_info(const sar_batch *batch, int32_t *n_jobs, int64_t *units, int32_t *ctas);
+
+/*
  * Whole frame from host memory: copy beat, w_sar and trajectory to the
  * plan's device staging buffers, range-compress, backproject and copy the
  * image back to image_host, all on `stream`; returns after the image is in

@@ -26,6 +26,8 @@ EXPORTS = (
     "sar_plan_create", "sar_plan_destroy", "sar_plan_get_info", "sar_profile_bytes",
     "sar_range_compress", "sar_range_spectrum", "sar_backproject", "sar_form_image_host",
     "sar_plan_check_errors", "sar_status_string", "sar_version", "sar_backproject_noalloc",
+    "sar_batch_create", "sar_batch_destroy", "sar_batch_clear", "sar_batch_add",
+    "sar_batch_commit", "sar_batch_launch", "sar_batch_get_info",
 )
 
 
@@ -89,13 +91,22 @@ def load_library(path: str = LIB_PATH):
     lib.sar_backproject.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32, vp]
     lib.sar_backproject_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32, vp]
     lib.sar_form_image_host.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
+    lib.sar_batch_create.argtypes = [i32, ctypes.POINTER(vp)]
+    lib.sar_batch_destroy.argtypes = [vp]
+    lib.sar_batch_destroy.restype = None
+    lib.sar_batch_clear.argtypes = [vp]
+    lib.sar_batch_add.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32]
+    lib.sar_batch_commit.argtypes = [vp, vp]
+    lib.sar_batch_launch.argtypes = [vp, vp]
+    lib.sar_batch_get_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(i32)]
     lib.sar_plan_check_errors.argtypes = [vp]
     lib.sar_status_string.argtypes = [ctypes.c_int]
     lib.sar_status_string.restype = ctypes.c_char_p
     lib.sar_version.argtypes = []
     for name in EXPORTS:
         fn = getattr(lib, name)
-        if name not in ("sar_plan_destroy", "sar_status_string"):
+        if name not in ("sar_plan_destroy", "sar_status_string", "sar_batch_destroy"):
             fn.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -257,3 +268,51 @@ class Plan:
 
     def check_errors(self) -> int:
         return self._lib.sar_plan_check_errors(self._plan)
+
+
+class Batch:
+    """A sar_batch: several backprojection requests in one persistent launch."""
+
+    def __init__(self, max_jobs: int):
+        self._lib = load_library()
+        self._b = None
+        h = ctypes.c_void_p()
+        _check(self._lib.sar_batch_create(max_jobs, ctypes.byref(h)), "sar_batch_create")
+        self._b = h
+        self._keep = []
+
+    def close(self):
+        if self._b is not None:
+            self._lib.sar_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def clear(self):
+        _check(self._lib.sar_batch_clear(self._b), "sar_batch_clear")
+        self._keep = []
+
+    def add(self, plan: "Plan", prof, M: int, q_tx, q_rx, image, accumulate: bool = False):
+        import torch
+        _require_cuda(q_tx, "q_tx", torch.float64)
+        _require_cuda(q_rx, "q_rx", torch.float64)
+        _require_cuda(image, "image", torch.complex64)
+        _check(self._lib.sar_batch_add(self._b, plan.handle, _ptr(prof), M, _ptr(q_tx), _ptr(q_rx),
+                                       _ptr(image), 1 if accumulate else 0), "sar_batch_add")
+        self._keep.append((plan, prof, q_tx, q_rx, image))
+
+    def commit(self, stream=None):
+        _check(self._lib.sar_batch_commit(self._b, _stream(stream)), "sar_batch_commit")
+
+    def launch(self, stream=None):
+        _check(self._lib.sar_batch_launch(self._b, _stream(stream)), "sar_batch_launch")
+
+    def info(self):
+        n, u, g = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+        _check(self._lib.sar_batch_get_info(self._b, ctypes.byref(n), ctypes.byref(u),
+                                            ctypes.byref(g)), "sar_batch_get_info")
+        return n.value, u.value, g.value

@@ -52,6 +52,24 @@ struct sar_plan {
     std::vector<void *> allocs;
 };
 
+struct sar_batch {
+    int device = 0;
+    int max_jobs = 0, n_jobs = 0;
+    int num_sms = 0, g_cap = 0, G = 0;
+    long long units = 0;
+    int tiles = 0;
+    size_t smem = 0;
+    bool committed = false, upload_pending = false;
+    BpArgs *h_jobs = nullptr;
+    long long *h_ub = nullptr;
+    int *h_tb = nullptr;
+    BpArgs *d_jobs = nullptr;
+    long long *d_ub = nullptr;
+    int *d_tb = nullptr;
+    float2 *d_scratch = nullptr;
+    cudaEvent_t uploaded = nullptr;
+};
+
 namespace {
 
 struct DeviceGuard {
@@ -343,7 +361,7 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
     int L = (int)std::ceil(span) + 2 * kGuardBins + 4;
     L = (L + 3) & ~3;
     pl->L = L;
-    pl->rg = (p.n_rx % 4 == 0) ? 4 : (p.n_rx % 2 == 0) ? 2 : 1;
+    pl->rg = (p.n_rx % 4 == 0) ? 4 : (p.n_rx % 3 == 0) ? 3 : (p.n_rx % 2 == 0) ? 2 : 1;
     const size_t per_pulse = bp_smem_bytes(1, p.n_rx, L, pl->fp16);
     int Mb = (int)std::min<size_t>(kMaxPulsesPerBlock, std::max<size_t>(1, kBpSmemTarget / per_pulse));
     while (Mb > 1 && bp_smem_bytes(Mb, p.n_rx, L, pl->fp16) > kBpSmemTarget) --Mb;
@@ -499,6 +517,58 @@ int bp_launch(sar_plan *pl, const void *prof, int M, const double *q_tx, const d
 namespace sar {
 
 int plan_device(const sar_plan *pl) { return pl->device; }
+
+// Kernel arguments of one backprojection request (no scratch; the batched
+// form supplies its own).
+int fill_bp_args(const sar_plan *pl, const void *prof, int M, const double *q_tx, const double *q_rx,
+                 void *image, int accumulate, BpArgs *out, size_t *smem) {
+    if (!pl || !prof || !q_tx || !q_rx || !image || M < 1 || M > pl->p.max_pulses) return SAR_EINVAL;
+    if (!aligned(prof, 256) || !aligned(q_tx, 16) || !aligned(q_rx, 16) || !aligned(image, 8)) return SAR_EINVAL;
+    BpArgs a{};
+    const size_t rows = (size_t)M * pl->p.n_rx;
+    if (pl->fp16) {
+        a.prof_scale = (const float *)prof;
+        a.prof = (const unsigned char *)prof + ((rows * 4 + 255) & ~size_t(255));
+    } else {
+        a.prof = prof;
+        a.prof_scale = nullptr;
+    }
+    a.q_tx = q_tx;
+    a.q_rx = q_rx;
+    a.fdopp = nullptr;
+    a.image = (float2 *)image;
+    a.partial = nullptr;
+    a.err = pl->d_err;
+    a.pix = pl->d_pix;
+    a.out_idx = pl->d_out;
+    a.tiles = pl->d_tiles;
+    a.M = M;
+    a.R = pl->p.n_rx;
+    a.n_tiles = pl->n_tiles;
+    a.Mb = pl->Mb;
+    a.L = pl->L;
+    a.blocks_per_tile = (M + pl->Mb - 1) / pl->Mb;
+    a.units = (long long)pl->n_tiles * a.blocks_per_tile;
+    a.G = 0;
+    a.seg_max = 0;
+    a.n_bins = pl->n_bins;
+    a.crop_lo = pl->crop_lo;
+    a.crop_hi = pl->crop_hi;
+    a.accumulate = accumulate ? 1 : 0;
+    a.a1 = pl->a1;
+    a.a1f = (float)pl->a1;
+    a.two_pi_beta = (float)(pl->sign * 2.0 * kPi * pl->beta);
+    a.beta = (float)pl->beta;
+    a.sign = (float)pl->sign;
+    const double cb = -pl->sign * 2.0 * kPi * (pl->beta - std::floor(pl->beta));
+    a.cb = make_float2((float)std::cos(cb), (float)std::sin(cb));
+    a.fd_max = pl->fd_max;
+    a.fp16 = pl->fp16 ? 1 : 0;
+    a.rg = pl->rg;
+    *out = a;
+    *smem = pl->bp_smem;
+    return SAR_OK;
+}
 
 // The launch of sar_backproject with the split-tile partial sums in
 // `scratch` (scratch_bytes long) instead of the plan's own buffer.  Returns
@@ -681,6 +751,145 @@ int sar_form_image_host(sar_plan *pl, const void *beat_host, int32_t M, const fl
     if (cudaMemcpyAsync(image_host, pl->s_img, (size_t)pl->n_pixels * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return SAR_ECUDA;
     return cudaStreamSynchronize(s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
+}
+
+int sar_batch_create(int32_t max_jobs, sar_batch **out) {
+    if (!out || max_jobs < 1 || max_jobs > (1 << 20)) return SAR_EINVAL;
+    *out = nullptr;
+    sar_batch *b = new (std::nothrow) sar_batch();
+    if (!b) return SAR_ENOMEM;
+    b->max_jobs = max_jobs;
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        delete b;
+        return SAR_ECUDA;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, b->device) != cudaSuccess) {
+        delete b;
+        return SAR_ECUDA;
+    }
+    b->num_sms = prop.multiProcessorCount;
+    b->g_cap = b->num_sms * 2;  // the batch kernel runs at most two CTAs per SM
+    bool ok = cudaMallocHost((void **)&b->h_jobs, sizeof(BpArgs) * max_jobs) == cudaSuccess &&
+              cudaMallocHost((void **)&b->h_ub, sizeof(long long) * (max_jobs + 1)) == cudaSuccess &&
+              cudaMallocHost((void **)&b->h_tb, sizeof(int) * (max_jobs + 1)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_jobs, sizeof(BpArgs) * max_jobs) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_ub, sizeof(long long) * (max_jobs + 1)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_tb, sizeof(int) * (max_jobs + 1)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_scratch, sizeof(float2) * kTilePx * 2 * (size_t)b->g_cap) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        sar_batch_destroy(b);
+        return SAR_ENOMEM;
+    }
+    *out = b;
+    return SAR_OK;
+}
+
+void sar_batch_destroy(sar_batch *b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->h_jobs) cudaFreeHost(b->h_jobs);
+    if (b->h_ub) cudaFreeHost(b->h_ub);
+    if (b->h_tb) cudaFreeHost(b->h_tb);
+    if (b->d_jobs) cudaFree(b->d_jobs);
+    if (b->d_ub) cudaFree(b->d_ub);
+    if (b->d_tb) cudaFree(b->d_tb);
+    if (b->d_scratch) cudaFree(b->d_scratch);
+    if (b->uploaded) cudaEventDestroy(b->uploaded);
+    delete b;
+}
+
+int sar_batch_clear(sar_batch *b) {
+    if (!b) return SAR_EINVAL;
+    // the host descriptor table may still be read by an upload in flight
+    if (b->upload_pending && cudaEventSynchronize(b->uploaded) != cudaSuccess) return SAR_ECUDA;
+    b->upload_pending = false;
+    b->n_jobs = 0;
+    b->units = 0;
+    b->tiles = 0;
+    b->smem = 0;
+    b->committed = false;
+    return SAR_OK;
+}
+
+int sar_batch_add(sar_batch *b, sar_plan *plan, const void *prof_dev, int32_t M, const double *q_tx_dev,
+                  const double *q_rx_dev, void *image_dev, int32_t accumulate) {
+    if (!b || !plan) return SAR_EINVAL;
+    if (b->n_jobs >= b->max_jobs || plan->device != b->device) return SAR_EINVAL;
+    if (b->upload_pending) {
+        if (cudaEventSynchronize(b->uploaded) != cudaSuccess) return SAR_ECUDA;
+        b->upload_pending = false;
+    }
+    BpArgs a;
+    size_t smem = 0;
+    const int rc = fill_bp_args(plan, prof_dev, M, q_tx_dev, q_rx_dev, image_dev, accumulate, &a, &smem);
+    if (rc) return rc;
+    b->h_jobs[b->n_jobs] = a;
+    b->h_ub[b->n_jobs] = b->units;
+    b->h_tb[b->n_jobs] = b->tiles;
+    b->units += a.units;
+    b->tiles += a.n_tiles;
+    b->smem = std::max(b->smem, smem);
+    b->n_jobs += 1;
+    b->committed = false;
+    return SAR_OK;
+}
+
+int sar_batch_commit(sar_batch *b, void *stream) {
+    if (!b) return SAR_EINVAL;
+    if (b->n_jobs == 0) {
+        b->committed = true;
+        return SAR_OK;
+    }
+    DeviceGuard dg(b->device);
+    if (!dg.ok) return SAR_ECUDA;
+    b->h_ub[b->n_jobs] = b->units;
+    b->h_tb[b->n_jobs] = b->tiles;
+    int occ = 0;
+    if (bp_batch_prepare(b->smem, &occ) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return SAR_ECUDA;
+    }
+    b->G = (int)std::min<long long>(std::min(b->g_cap, b->num_sms * occ), b->units);
+    cudaStream_t s = (cudaStream_t)stream;
+    bool ok = cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(BpArgs) * b->n_jobs, cudaMemcpyHostToDevice, s) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(b->d_ub, b->h_ub, sizeof(long long) * (b->n_jobs + 1), cudaMemcpyHostToDevice, s) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(b->d_tb, b->h_tb, sizeof(int) * (b->n_jobs + 1), cudaMemcpyHostToDevice, s) ==
+                  cudaSuccess &&
+              cudaEventRecord(b->uploaded, s) == cudaSuccess;
+    if (!ok) return SAR_ECUDA;
+    b->upload_pending = true;
+    b->committed = true;
+    return SAR_OK;
+}
+
+int sar_batch_launch(sar_batch *b, void *stream) {
+    if (!b || !b->committed) return SAR_EINVAL;
+    if (b->n_jobs == 0) return SAR_OK;
+    DeviceGuard dg(b->device);
+    if (!dg.ok) return SAR_ECUDA;
+    BpBatchArgs a{};
+    a.jobs = b->d_jobs;
+    a.unit_begin = b->d_ub;
+    a.tile_begin = b->d_tb;
+    a.scratch = b->d_scratch;
+    a.units = b->units;
+    a.n_jobs = b->n_jobs;
+    a.G = b->G;
+    return launch_backproject_batch(a, b->tiles, b->smem, (cudaStream_t)stream) == cudaSuccess ? SAR_OK
+                                                                                                 : SAR_ECUDA;
+}
+
+int sar_batch_get_info(const sar_batch *b, int32_t *n_jobs, int64_t *units, int32_t *ctas) {
+    if (!b) return SAR_EINVAL;
+    if (n_jobs) *n_jobs = b->n_jobs;
+    if (units) *units = b->units;
+    if (ctas) *ctas = b->G;
+    return SAR_OK;
 }
 
 int sar_plan_check_errors(sar_plan *pl) {

@@ -371,7 +371,60 @@ __device__ __forceinline__ void accumulate(float idx, uint32_t ac, float k2pb, f
     acc_im = fmaf(vim, cs, acc_im);
 }
 
-// Expansion loop over one pulse block (far field, small Rx offsets).
+// PU consecutive pulses of the expansion loop, unrolled together so that
+// RG x PU x 4 updates per thread are independent (latency hiding for small
+// Rx counts).
+template <int RG, int PU, bool FD>
+__device__ __forceinline__ void expand_pulses(const BpArgs &a, const float4 *txr, const int4 *txc,
+                                              const float4 *rxt, int p,
+                                              const float (&dx)[kPxPerThread],
+                                              const float (&dy)[kPxPerThread],
+                                              const float (&hd2)[kPxPerThread],
+                                              const float (&fdi)[kPxPerThread],
+                                              float (&acc_re)[kPxPerThread],
+                                              float (&acc_im)[kPxPerThread]) {
+    const int R = a.R;
+    const float a1 = a.a1f, two_a1 = 2.0f * a.a1f, half_a1 = 0.5f * a.a1f;
+    const float k2pb = a.two_pi_beta;
+    float u[PU][kPxPerThread], ay[PU][kPxPerThread], kk[PU][kPxPerThread];
+#pragma unroll
+    for (int q = 0; q < PU; ++q) {
+        const float4 t4 = txr[p + q];
+        const float cidx = __int_as_float(txc[p + q].x);
+#pragma unroll
+        for (int j = 0; j < kPxPerThread; ++j) {
+            float y;
+            const float dt = range_delta(t4, dx[j], dy[j], hd2[j], y);
+            // index of the Tx part (twice the Tx range) and the expansion
+            // coefficients a1/d and a1/(2 d^3)
+            u[q][j] = fmaf(two_a1, dt, FD ? cidx + fdi[j] : cidx);
+            ay[q][j] = a1 * y;
+            kk[q][j] = (half_a1 * y) * (y * y);
+        }
+    }
+    for (int r0 = 0; r0 < R; r0 += RG) {
+#pragma unroll
+        for (int q = 0; q < PU; ++q) {
+#pragma unroll
+            for (int rr = 0; rr < RG; ++rr) {
+                const float4 o4 = rxt[(p + q) * R + r0 + rr];
+                const uint32_t ac = __float_as_uint(o4.w);
+#pragma unroll
+                for (int j = 0; j < kPxPerThread; ++j) {
+                    // a = |o|^2/2 - (p - q_tx).o;  a1 (d_rx - d_tx) = a (a1/d - a a1/(2 d^3))
+                    const float av = fmaf(o4.x, dx[j], fmaf(o4.y, dy[j], o4.z));
+                    const float m1 = fmaf(-av, kk[q][j], ay[q][j]);
+                    const float idx = fmaf(av, m1, u[q][j]);
+                    accumulate(idx, ac, k2pb, acc_re[j], acc_im[j]);
+                }
+            }
+        }
+    }
+}
+
+// Expansion loop over one pulse block (far field, small Rx offsets).  When
+// all Rx channels of a pulse fit one group (R == RG < 3), 4 / RG pulses are
+// processed together; the per-pixel summation order stays pulse by pulse.
 template <int RG, bool FD>
 __device__ __forceinline__ void compute_block_expand(const BpArgs &a, const Smem &sm, int b, int cslot,
                                                      const float (&dx)[kPxPerThread],
@@ -380,43 +433,18 @@ __device__ __forceinline__ void compute_block_expand(const BpArgs &a, const Smem
                                                      const float (&fdi)[kPxPerThread],
                                                      float (&acc_re)[kPxPerThread],
                                                      float (&acc_im)[kPxPerThread]) {
+    constexpr int PU = RG >= 3 ? 1 : 4 / RG;
     const int R = a.R, Mb = a.Mb, MbR = Mb * R;
     const int np = min(Mb, a.M - b * Mb);
     const float4 *txr = sm.txr(cslot, Mb);
     const int4 *txc = sm.txc(cslot, Mb);
     const float4 *rxt = sm.rxt(cslot, MbR);
-    const float a1 = a.a1f, two_a1 = 2.0f * a.a1f, half_a1 = 0.5f * a.a1f;
-    const float k2pb = a.two_pi_beta;
-    for (int p = 0; p < np; ++p) {
-        const float4 t4 = txr[p];
-        const float cidx = __int_as_float(txc[p].x);
-        float u[kPxPerThread], ay[kPxPerThread], kk[kPxPerThread];
-#pragma unroll
-        for (int j = 0; j < kPxPerThread; ++j) {
-            float y;
-            const float dt = range_delta(t4, dx[j], dy[j], hd2[j], y);
-            // index of the Tx part (twice the Tx range) and the expansion
-            // coefficients a1/d and a1/(2 d^3)
-            u[j] = fmaf(two_a1, dt, FD ? cidx + fdi[j] : cidx);
-            ay[j] = a1 * y;
-            kk[j] = (half_a1 * y) * (y * y);
-        }
-        for (int r0 = 0; r0 < R; r0 += RG) {
-#pragma unroll
-            for (int rr = 0; rr < RG; ++rr) {
-                const float4 o4 = rxt[p * R + r0 + rr];
-                const uint32_t ac = __float_as_uint(o4.w);
-#pragma unroll
-                for (int j = 0; j < kPxPerThread; ++j) {
-                    // a = |o|^2/2 - (p - q_tx).o;  a1 (d_rx - d_tx) = a (a1/d - a a1/(2 d^3))
-                    const float av = fmaf(o4.x, dx[j], fmaf(o4.y, dy[j], o4.z));
-                    const float m1 = fmaf(-av, kk[j], ay[j]);
-                    const float idx = fmaf(av, m1, u[j]);
-                    accumulate(idx, ac, k2pb, acc_re[j], acc_im[j]);
-                }
-            }
-        }
+    int p = 0;
+    if (PU > 1 && R == RG) {
+        for (; p + PU <= np; p += PU)
+            expand_pulses<RG, PU, FD>(a, txr, txc, rxt, p, dx, dy, hd2, fdi, acc_re, acc_im);
     }
+    for (; p < np; ++p) expand_pulses<RG, 1, FD>(a, txr, txc, rxt, p, dx, dy, hd2, fdi, acc_re, acc_im);
 }
 
 // Exact loop over one pulse block: every distance from its own rsqrt and
@@ -467,6 +495,104 @@ __device__ __forceinline__ void compute_block_exact(const BpArgs &a, const Smem 
     }
 }
 
+// One segment of a CTA's work: pulse blocks [b0, b1) of one tile, from the
+// pixel load through the pipeline to the output write.  partial_dst == null:
+// the segment covers the whole tile and writes (or adds to) the image;
+// otherwise it writes its partial sums there for the fix-up kernel.
+template <int RG, bool FP16, bool FD>
+__device__ __forceinline__ void process_segment(const BpArgs &a, const Smem &sm, int tile, int b0, int b1,
+                                                float2 *partial_dst) {
+    const TileInfo ti = a.tiles[tile];
+
+    float dx[kPxPerThread], dy[kPxPerThread], hd2[kPxPerThread], fdi[kPxPerThread];
+    int oi[kPxPerThread];
+    float acc_re[kPxPerThread], acc_im[kPxPerThread];
+#pragma unroll
+    for (int j = 0; j < kPxPerThread; ++j) {
+        const long long slot = (long long)tile * kTilePx + threadIdx.x + j * kBpThreads;
+        const float2 d = a.pix[slot];
+        oi[j] = a.out_idx[slot];
+        dx[j] = d.x;
+        dy[j] = d.y;
+        hd2[j] = 0.5f * fmaf(d.x, d.x, d.y * d.y);
+        fdi[j] = 0.f;
+        if (FD && oi[j] >= 0) fdi[j] = fminf(fmaxf(a.fdopp[oi[j]], -a.fd_max), a.fd_max);
+        acc_re[j] = 0.f;
+        acc_im[j] = 0.f;
+    }
+
+    // pipeline prologue; the loop choices (exact or expansion) of blocks
+    // b, b+1, b+2 are block-uniform (reduced by the barriers)
+    int fl = prep_block(a, sm, ti, b0, 0, 0);
+    if (b0 + 1 < b1) fl |= prep_block(a, sm, ti, b0 + 1, 1, 1) << 1;
+    int ex_cur = __syncthreads_or(fl & 1);
+    int ex_next = __syncthreads_or(fl & 2) ? 1 : 0;
+    if (ex_cur) {
+        prep_exact(a, sm, ti, b0, 0, 0);
+        __syncthreads();
+    }
+    stage_block<FP16>(a, sm, b0, 0, ex_cur);
+    cp_async_commit();
+    cp_async_wait_all();
+    convert_block<FP16>(a, sm, b0, 0, 0, ex_cur);
+    __syncthreads();
+
+    for (int b = b0; b < b1; ++b) {
+        const int k = b - b0;
+        int ex_new = 0;
+        if (b + 2 < b1) ex_new = prep_block(a, sm, ti, b + 2, (k + 2) % 3, (k + 2) & 1);
+        if (b + 1 < b1 && ex_next) {  // block-uniform
+            prep_exact(a, sm, ti, b + 1, (k + 1) % 3, (k + 1) & 1);
+            __syncthreads();
+        }
+        if (b + 1 < b1) stage_block<FP16>(a, sm, b + 1, (k + 1) % 3, ex_next);
+        cp_async_commit();
+        if (ex_cur)
+            compute_block_exact<RG, FD>(a, sm, b, k % 3, dx, dy, hd2, fdi, acc_re, acc_im);
+        else
+            compute_block_expand<RG, FD>(a, sm, b, k % 3, dx, dy, hd2, fdi, acc_re, acc_im);
+        cp_async_wait_all();
+        if (b + 1 < b1) convert_block<FP16>(a, sm, b + 1, (k + 1) % 3, (k + 1) & 1, ex_next);
+        ex_new = __syncthreads_or(ex_new);
+        ex_cur = ex_next;
+        ex_next = ex_new;
+    }
+
+    if (FD) {
+        // the Doppler offset moved the index, not the phase: undo its share
+        // exp(sign j 2 pi beta f_doppler) of the per-index phase
+#pragma unroll
+        for (int j = 0; j < kPxPerThread; ++j) {
+            float cyc = a.beta * fdi[j];
+            cyc -= rintf(cyc);
+            float sn, cs;
+            sincospif(-2.0f * a.sign * cyc, &sn, &cs);
+            const float re = acc_re[j] * cs - acc_im[j] * sn;
+            const float im = acc_re[j] * sn + acc_im[j] * cs;
+            acc_re[j] = re;
+            acc_im[j] = im;
+        }
+    }
+
+    if (partial_dst == nullptr) {
+#pragma unroll
+        for (int j = 0; j < kPxPerThread; ++j) {
+            if (oi[j] < 0) continue;
+            float2 v = make_float2(acc_re[j], acc_im[j]);
+            if (a.accumulate) {
+                const float2 o = a.image[oi[j]];
+                v.x += o.x;
+                v.y += o.y;
+            }
+            a.image[oi[j]] = v;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPxPerThread; ++j)
+            partial_dst[threadIdx.x + j * kBpThreads] = make_float2(acc_re[j], acc_im[j]);
+    }
+}
+
 template <int RG, bool FP16, bool FD>
 __global__ void __launch_bounds__(kBpThreads, 2) backproject_kernel(BpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_bp[];
@@ -485,98 +611,93 @@ __global__ void __launch_bounds__(kBpThreads, 2) backproject_kernel(BpArgs a) {
         const int tile = (int)(u / PB);
         const int b0 = (int)(u - (long long)tile * PB);
         const int b1 = (int)min((long long)PB, (long long)b0 + (u1 - u));
-        const TileInfo ti = a.tiles[tile];
+        float2 *dst = nullptr;
+        if (!(b0 == 0 && b1 == PB))
+            dst = a.partial + ((long long)blockIdx.x * a.seg_max + (tile - t_first)) * kTilePx;
+        process_segment<RG, FP16, FD>(a, sm, tile, b0, b1, dst);
+        u += b1 - b0;
+    }
+}
 
-        float dx[kPxPerThread], dy[kPxPerThread], hd2[kPxPerThread], fdi[kPxPerThread];
-        int oi[kPxPerThread];
-        float acc_re[kPxPerThread], acc_im[kPxPerThread];
-#pragma unroll
-        for (int j = 0; j < kPxPerThread; ++j) {
-            const long long slot = (long long)tile * kTilePx + threadIdx.x + j * kBpThreads;
-            const float2 d = a.pix[slot];
-            oi[j] = a.out_idx[slot];
-            dx[j] = d.x;
-            dy[j] = d.y;
-            hd2[j] = 0.5f * fmaf(d.x, d.x, d.y * d.y);
-            fdi[j] = 0.f;
-            if (FD && oi[j] >= 0) fdi[j] = fminf(fmaxf(a.fdopp[oi[j]], -a.fd_max), a.fd_max);
-            acc_re[j] = 0.f;
-            acc_im[j] = 0.f;
-        }
-
-        // pipeline prologue; the loop choices (exact or expansion) of blocks
-        // b, b+1, b+2 are block-uniform (reduced by the barriers)
-        int fl = prep_block(a, sm, ti, b0, 0, 0);
-        if (b0 + 1 < b1) fl |= prep_block(a, sm, ti, b0 + 1, 1, 1) << 1;
-        int ex_cur = __syncthreads_or(fl & 1);
-        int ex_next = __syncthreads_or(fl & 2) ? 1 : 0;
-        if (ex_cur) {
-            prep_exact(a, sm, ti, b0, 0, 0);
-            __syncthreads();
-        }
-        stage_block<FP16>(a, sm, b0, 0, ex_cur);
-        cp_async_commit();
-        cp_async_wait_all();
-        convert_block<FP16>(a, sm, b0, 0, 0, ex_cur);
-        __syncthreads();
-
-        for (int b = b0; b < b1; ++b) {
-            const int k = b - b0;
-            int ex_new = 0;
-            if (b + 2 < b1) ex_new = prep_block(a, sm, ti, b + 2, (k + 2) % 3, (k + 2) & 1);
-            if (b + 1 < b1 && ex_next) {  // block-uniform
-                prep_exact(a, sm, ti, b + 1, (k + 1) % 3, (k + 1) & 1);
-                __syncthreads();
-            }
-            if (b + 1 < b1) stage_block<FP16>(a, sm, b + 1, (k + 1) % 3, ex_next);
-            cp_async_commit();
-            if (ex_cur)
-                compute_block_exact<RG, FD>(a, sm, b, k % 3, dx, dy, hd2, fdi, acc_re, acc_im);
-            else
-                compute_block_expand<RG, FD>(a, sm, b, k % 3, dx, dy, hd2, fdi, acc_re, acc_im);
-            cp_async_wait_all();
-            if (b + 1 < b1) convert_block<FP16>(a, sm, b + 1, (k + 1) % 3, (k + 1) & 1, ex_next);
-            ex_new = __syncthreads_or(ex_new);
-            ex_cur = ex_next;
-            ex_next = ex_new;
-        }
-
-        if (FD) {
-            // the Doppler offset moved the index, not the phase: undo its share
-            // exp(sign j 2 pi beta f_doppler) of the per-index phase
-#pragma unroll
-            for (int j = 0; j < kPxPerThread; ++j) {
-                float cyc = a.beta * fdi[j];
-                cyc -= rintf(cyc);
-                float sn, cs;
-                sincospif(-2.0f * a.sign * cyc, &sn, &cs);
-                const float re = acc_re[j] * cs - acc_im[j] * sn;
-                const float im = acc_re[j] * sn + acc_im[j] * cs;
-                acc_re[j] = re;
-                acc_im[j] = im;
-            }
-        }
-
-        if (b0 == 0 && b1 == PB) {
-#pragma unroll
-            for (int j = 0; j < kPxPerThread; ++j) {
-                if (oi[j] < 0) continue;
-                float2 v = make_float2(acc_re[j], acc_im[j]);
-                if (a.accumulate) {
-                    const float2 o = a.image[oi[j]];
-                    v.x += o.x;
-                    v.y += o.y;
-                }
-                a.image[oi[j]] = v;
-            }
+// Batched form: the (request, tile, pulse block) units of several requests,
+// each with its own plan, profiles, trajectory and image, concatenated and
+// split into equal contiguous ranges over one persistent grid.  Only the
+// first and the last segment of a CTA's range can cover part of a tile, so
+// each CTA owns two partial-sum slots (0: first segment, 1: last segment).
+__global__ void __launch_bounds__(kBpThreads, 2) backproject_batch_kernel(BpBatchArgs B) {
+    extern __shared__ __align__(16) unsigned char smem_bp[];
+    Smem sm;
+    sm.base = smem_bp;
+    sm.base_addr = (uint32_t)__cvta_generic_to_shared(smem_bp);
+    const long long u0 = (long long)blockIdx.x * B.units / B.G;
+    const long long u1 = (long long)(blockIdx.x + 1) * B.units / B.G;
+    // job holding u0: the last j with unit_begin[j] <= u0
+    int lo = 0, hi = B.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.unit_begin[mid] <= u0) lo = mid; else hi = mid - 1;
+    }
+    int j = lo;
+    long long u = u0;
+    while (u < u1) {
+        while (u >= B.unit_begin[j + 1]) ++j;
+        const BpArgs a = B.jobs[j];
+        sm.lay = bp_layout(a.Mb, a.R, a.L, a.fp16 != 0);
+        const long long v = u - B.unit_begin[j];
+        const int PB = a.blocks_per_tile;
+        const int tile = (int)(v / PB);
+        const int b0 = (int)(v - (long long)tile * PB);
+        const int b1 = (int)min((long long)PB, (long long)b0 + (u1 - u));
+        float2 *dst = nullptr;
+        if (!(b0 == 0 && b1 == PB)) dst = B.scratch + ((long long)blockIdx.x * 2 + (u == u0 ? 0 : 1)) * kTilePx;
+        if (a.fp16) {
+            if (a.rg == 4) process_segment<4, true, false>(a, sm, tile, b0, b1, dst);
+            else if (a.rg == 3) process_segment<3, true, false>(a, sm, tile, b0, b1, dst);
+            else if (a.rg == 2) process_segment<2, true, false>(a, sm, tile, b0, b1, dst);
+            else process_segment<1, true, false>(a, sm, tile, b0, b1, dst);
         } else {
-            const long long slot = (long long)blockIdx.x * a.seg_max + (tile - t_first);
-            float2 *dst = a.partial + slot * kTilePx;
-#pragma unroll
-            for (int j = 0; j < kPxPerThread; ++j)
-                dst[threadIdx.x + j * kBpThreads] = make_float2(acc_re[j], acc_im[j]);
+            if (a.rg == 4) process_segment<4, false, false>(a, sm, tile, b0, b1, dst);
+            else if (a.rg == 3) process_segment<3, false, false>(a, sm, tile, b0, b1, dst);
+            else if (a.rg == 2) process_segment<2, false, false>(a, sm, tile, b0, b1, dst);
+            else process_segment<1, false, false>(a, sm, tile, b0, b1, dst);
         }
         u += b1 - b0;
+    }
+}
+
+// Fix-up of the batched form: one CTA per tile of every request.
+__global__ void __launch_bounds__(256) bp_batch_fixup_kernel(BpBatchArgs B) {
+    const int gt = blockIdx.x;
+    int lo = 0, hi = B.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.tile_begin[mid] <= gt) lo = mid; else hi = mid - 1;
+    }
+    const BpArgs &a = B.jobs[lo];
+    const int tile = gt - B.tile_begin[lo];
+    const long long PB = a.blocks_per_tile;
+    const long long tb = B.unit_begin[lo] + (long long)tile * PB;
+    const long long te = tb + PB;
+    const int ia = (int)(((tb + 1) * B.G - 1) / B.units);
+    const int ib = (int)((te * B.G - 1) / B.units);
+    if (ia == ib) return;
+    for (int s = threadIdx.x; s < kTilePx; s += blockDim.x) {
+        const int o = a.out_idx[(long long)tile * kTilePx + s];
+        if (o < 0) continue;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int i = ia; i <= ib; ++i) {
+            const long long ui0 = (long long)i * B.units / B.G;
+            const long long slot = (long long)i * 2 + (ui0 >= tb ? 0 : 1);
+            const float2 v = B.scratch[slot * kTilePx + s];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        if (a.accumulate) {
+            const float2 old = a.image[o];
+            acc.x += old.x;
+            acc.y += old.y;
+        }
+        a.image[o] = acc;
     }
 }
 
@@ -622,6 +743,7 @@ void *select_kernel(int rg, bool fp16, bool fd) {
     }
     SAR_SEL(1)
     SAR_SEL(2)
+    SAR_SEL(3)
     SAR_SEL(4)
 #undef SAR_SEL
     return nullptr;
@@ -631,11 +753,17 @@ void *select_kernel(int rg, bool fp16, bool fd) {
 
 size_t bp_smem_bytes(int Mb, int R, int L, bool fp16) { return bp_layout(Mb, R, L, fp16).total; }
 
+// The dynamic shared-memory limit is a per-kernel, process-wide attribute:
+// plans (and batches) of different sizes share the kernels, so it is raised
+// once to the largest size any of them may use, never lowered.
+constexpr int kSmemLimit = 227 * 1024;
+
 cudaError_t bp_prepare(bool fp16, int rg, size_t smem) {
+    if (smem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
     for (int fd = 0; fd < 2; ++fd) {
         void *k = select_kernel(rg, fp16, fd != 0);
         if (!k) return cudaErrorInvalidValue;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -648,6 +776,23 @@ int bp_occupancy(bool fp16, int rg, size_t smem, int *ctas_per_sm) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kBpThreads, smem) != cudaSuccess) return -1;
     *ctas_per_sm = n;
     return 0;
+}
+
+cudaError_t bp_batch_prepare(size_t smem, int *ctas_per_sm) {
+    if (smem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(backproject_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemLimit);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, backproject_batch_kernel, kBpThreads, smem);
+}
+
+cudaError_t launch_backproject_batch(const BpBatchArgs &b, int total_tiles, size_t smem, cudaStream_t s) {
+    if (b.units == 0 || b.n_jobs == 0) return cudaSuccess;
+    backproject_batch_kernel<<<b.G, kBpThreads, smem, s>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bp_batch_fixup_kernel<<<total_tiles, 256, 0, s>>>(b);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_backproject(const BpArgs &a, const BpLaunch &l, cudaStream_t s) {

@@ -230,7 +230,9 @@ cudaError_t launch_rc(const RcArgs &a, cudaStream_t s) {
     const int threads = T * rows_per_cta;
     const size_t smem = (size_t)rows_per_cta * (n + n / 16) * sizeof(float2);
     auto kern = n > 4096 ? range_compress_kernel<SGN, MODE, true> : range_compress_kernel<SGN, MODE, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // process-wide attribute shared by all plans: set to the largest row size
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(16384 * 17 / 16 * sizeof(float2)));
     if (e != cudaSuccess) return e;
     const long long blocks = (a.rows + rows_per_cta - 1) / rows_per_cta;
     if (blocks == 0) return cudaSuccess;

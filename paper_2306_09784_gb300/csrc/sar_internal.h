@@ -75,10 +75,24 @@ struct BpArgs {
     float sign;
     float2 cb;                 // exp(-sign j 2 pi beta)
     float fd_max;              // bound on |f_doppler|
+    int fp16;                  // profile storage (batched form)
+    int rg;                    // Rx group of the inner loop (batched form)
+};
+
+// Batched form: several requests (each a BpArgs with its own plan data)
+// backprojected by one persistent launch.
+struct BpBatchArgs {
+    const BpArgs *jobs;          // [n_jobs]
+    const long long *unit_begin; // [n_jobs + 1] prefix sums of (tile, pulse block) units
+    const int *tile_begin;       // [n_jobs + 1] prefix sums of tiles
+    float2 *scratch;             // [G * 2][kTilePx] partial sums
+    long long units;
+    int n_jobs;
+    int G;
 };
 
 struct BpLaunch {
-    int rg;       // Rx group size of the inner loop (1, 2 or 4)
+    int rg;       // Rx group size of the inner loop (1, 2, 3 or 4)
     bool fp16;
     size_t smem;  // dynamic shared memory bytes
 };
@@ -87,6 +101,8 @@ size_t bp_smem_bytes(int Mb, int R, int L, bool fp16);
 cudaError_t bp_prepare(bool fp16, int rg, size_t smem);  // sets function attributes
 int bp_occupancy(bool fp16, int rg, size_t smem, int *ctas_per_sm);
 cudaError_t launch_backproject(const BpArgs &a, const BpLaunch &l, cudaStream_t s);
+cudaError_t bp_batch_prepare(size_t smem, int *ctas_per_sm);
+cudaError_t launch_backproject_batch(const BpBatchArgs &b, int total_tiles, size_t smem, cudaStream_t s);
 
 // Used by sar_backproject_noalloc (noalloc.cu).
 int plan_device(const sar_plan *pl);

@@ -326,3 +326,29 @@ def azimuth_weights(n_pulses: int, kind: str = "hann") -> np.ndarray:
     if kind == "rect":
         return np.ones(n_pulses)
     return np.hanning(n_pulses) if n_pulses > 1 else np.ones(1)
+
+
+def make_batched_requests(n: int = 64, seed: int = 0, n_targets: int = 20,
+                          m_range=(128, 1024), side_range=(128, 768), rx_range=(1, 4),
+                          n_samples: int = 512):
+    """Uneven sub-aperture requests for the batched form: seeded pulse counts,
+    square image sides (multiples of 16 px at 2.5 cm from y = 2 m), Rx counts,
+    trajectories (+-2 cm jitter) and point-scatterer scenes (Rayleigh
+    amplitudes, 20 dB AWGN).  Returns a list of Workload."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        M = int(rng.integers(m_range[0], m_range[1] + 1))
+        side = int(rng.integers(side_range[0] // 16, side_range[1] // 16 + 1)) * 16
+        R = int(rng.integers(rx_range[0], rx_range[1] + 1))
+        radar = Radar(n_samples=n_samples, n_rx=R, os=4)
+        grid = centred_grid(side, side, 0.025, 2.0)
+        q_tx, q_rx = trajectory(radar, M, jitter=0.02, rng=rng)
+        xlo, xhi = grid.x0, grid.x0 + grid.dx * (grid.nx - 1)
+        ylo, yhi = grid.y0, grid.y0 + grid.dy * (grid.ny - 1)
+        tg = np.stack([rng.uniform(xlo, xhi, n_targets), rng.uniform(ylo, yhi, n_targets)], 1)
+        am = rng.rayleigh(1.0, n_targets) * np.exp(1j * rng.uniform(0, 2 * np.pi, n_targets))
+        out.append(Workload(name=f"batch{i}", radar=radar, n_pulses=M, grid=grid, q_tx=q_tx,
+                            q_rx=q_rx, targets=tg, amps=am, snr_db=20.0, seed=seed * 1000 + i,
+                            crop=crop_for(radar, grid, q_tx, q_rx)))
+    return out
