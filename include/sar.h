@@ -259,6 +259,76 @@ int sar_batch_launch(sar_batch *batch, void *stream);
 int sar_batch_get_info(const sar_batch *batch, int32_t *n_jobs, int64_t *units, int32_t *ctas);
 
 /*
+ * Served form: continuous batching of imaging requests from several radars.
+ * A server owns one worker thread and three CUDA streams on the device that
+ * is current at creation.  Each request is one frame (sar_request): its beat
+ * cube, w_sar and trajectory are copied to the device when it is admitted,
+ * range-compressed, then backprojected in rounds: every round is ONE
+ * persistent batched launch over the next chunk_pulses chirps of every
+ * active request, accumulated into the request's device-resident image.
+ * Requests that arrive while a round runs join the next round; finished ones
+ * leave.  Admission is bounded by max_inflight and by an HBM budget (one
+ * device pool allocated at creation and sub-allocated per request); a request
+ * waits in arrival order until its buffers fit.  A request's image equals its
+ * stand-alone sar_range_compress + sar_backproject result up to FP32
+ * summation order.
+ *
+ * The caller keeps the plan and the host buffers of a request alive and
+ * unchanged until the request is DONE, FAILED or released.  Host buffers
+ * should be pinned (cudaHostAlloc) for asynchronous copies.
+ */
+enum sar_request_state {
+    SAR_REQ_QUEUED = 0,   /* waiting for admission */
+    SAR_REQ_RUNNING = 1,  /* on the device */
+    SAR_REQ_DONE = 2,     /* image complete (and copied to image_host if given) */
+    SAR_REQ_FAILED = 3    /* a CUDA error stopped the server */
+};
+
+typedef struct sar_server_config {
+    size_t hbm_budget_bytes;  /* device pool for request buffers (>= 1 MiB) */
+    int32_t max_inflight;     /* requests on the device at once (1..4096) */
+    int32_t queue_capacity;   /* submitted, not yet admitted (SAR_EAGAIN beyond) */
+    int32_t chunk_pulses;     /* chirps per request per round */
+    int32_t reserved;
+} sar_server_config;
+
+typedef struct sar_request {
+    sar_plan *plan;           /* radar parameters and reconstruction points */
+    const void *beat_host;    /* complex64 [M][R][N] */
+    int32_t M;                /* chirps (1..plan max_pulses) */
+    const float *w_az_host;   /* float [M] or NULL */
+    const double *q_tx_host;  /* double [M][2] */
+    const double *q_rx_host;  /* double [M][R][2] */
+    void *image_host;         /* complex64 [n_pixels] destination, or NULL (device only) */
+} sar_request;
+
+typedef struct sar_server_stats {
+    int32_t queued, active;
+    int64_t rounds, completed;
+    size_t pool_bytes;
+} sar_server_stats;
+
+typedef struct sar_server sar_server;
+
+int sar_server_create(const sar_server_config *cfg, sar_server **out);
+/* Stops the worker (after its queued GPU work drains) and frees everything. */
+void sar_server_destroy(sar_server *server);
+/* Queue a request.  SAR_EAGAIN: queue full; SAR_ENOMEM: it can never fit the
+ * budget; SAR_EINVAL: bad request.  *ticket identifies it afterwards. */
+int sar_submit(sar_server *server, const sar_request *req, uint64_t *ticket);
+/* Non-blocking: SAR_OK when done (image_dev valid until sar_release,
+ * latency_ms = submit to image ready), SAR_EAGAIN while queued or running,
+ * the failure status if failed, SAR_ENOTFOUND for an unknown ticket. */
+int sar_poll(sar_server *server, uint64_t ticket, int32_t *state, const void **image_dev,
+             double *latency_ms);
+/* Block until done or failed; SAR_ETIMEOUT after timeout_ms. */
+int sar_wait(sar_server *server, uint64_t ticket, double timeout_ms);
+/* Forget a request: frees its device image.  A queued request is dropped; a
+ * running one is cancelled and freed once its GPU work has drained. */
+int sar_release(sar_server *server, uint64_t ticket);
+int sar_server_get_stats(sar_server *server, sar_server_stats *stats);
+
+/*
  * Whole frame from host memory: copy beat, w_sar and trajectory to the
  * plan's device staging buffers, range-compress, backproject and copy the
  * image back to image_host, all on `stream`; returns after the image is in

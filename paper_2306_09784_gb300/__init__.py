@@ -28,7 +28,10 @@ EXPORTS = (
     "sar_plan_check_errors", "sar_status_string", "sar_version", "sar_backproject_noalloc",
     "sar_batch_create", "sar_batch_destroy", "sar_batch_clear", "sar_batch_add",
     "sar_batch_commit", "sar_batch_launch", "sar_batch_get_info",
+    "sar_server_create", "sar_server_destroy", "sar_submit", "sar_poll", "sar_wait",
+    "sar_release", "sar_server_get_stats",
 )
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 
 
 class SarError(RuntimeError):
@@ -67,6 +70,23 @@ class PlanInfo(ctypes.Structure):
     ]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
+                ("queue_capacity", ctypes.c_int32), ("chunk_pulses", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class RequestDesc(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("beat_host", ctypes.c_void_p), ("M", ctypes.c_int32),
+                ("w_az_host", ctypes.c_void_p), ("q_tx_host", ctypes.c_void_p),
+                ("q_rx_host", ctypes.c_void_p), ("image_host", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int32), ("active", ctypes.c_int32), ("rounds", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("pool_bytes", ctypes.c_size_t)]
+
+
 _lib = None
 
 
@@ -91,6 +111,15 @@ def load_library(path: str = LIB_PATH):
     lib.sar_backproject.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32, vp]
     lib.sar_backproject_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32, vp]
     lib.sar_form_image_host.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
+    lib.sar_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    lib.sar_server_destroy.argtypes = [vp]
+    lib.sar_server_destroy.restype = None
+    lib.sar_submit.argtypes = [vp, ctypes.POINTER(RequestDesc), ctypes.POINTER(ctypes.c_uint64)]
+    lib.sar_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32), ctypes.POINTER(vp),
+                             ctypes.POINTER(ctypes.c_double)]
+    lib.sar_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double]
+    lib.sar_release.argtypes = [vp, ctypes.c_uint64]
+    lib.sar_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
     lib.sar_batch_create.argtypes = [i32, ctypes.POINTER(vp)]
     lib.sar_batch_destroy.argtypes = [vp]
     lib.sar_batch_destroy.restype = None
@@ -106,7 +135,8 @@ def load_library(path: str = LIB_PATH):
     lib.sar_version.argtypes = []
     for name in EXPORTS:
         fn = getattr(lib, name)
-        if name not in ("sar_plan_destroy", "sar_status_string", "sar_batch_destroy"):
+        if name not in ("sar_plan_destroy", "sar_status_string", "sar_batch_destroy",
+                        "sar_server_destroy"):
             fn.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -316,3 +346,63 @@ class Batch:
         _check(self._lib.sar_batch_get_info(self._b, ctypes.byref(n), ctypes.byref(u),
                                             ctypes.byref(g)), "sar_batch_get_info")
         return n.value, u.value, g.value
+
+
+class Server:
+    """A sar_server: continuous batching of frames from several radars.
+
+    Host tensors passed to submit() (pinned for asynchronous copies) are kept
+    referenced until the request is released."""
+
+    def __init__(self, hbm_budget: int, max_inflight: int = 64, queue_capacity: int = 1024,
+                 chunk_pulses: int = 256):
+        self._lib = load_library()
+        self._s = None
+        cfg = ServerConfig(hbm_budget_bytes=hbm_budget, max_inflight=max_inflight,
+                           queue_capacity=queue_capacity, chunk_pulses=chunk_pulses, reserved=0)
+        h = ctypes.c_void_p()
+        _check(self._lib.sar_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sar_server_create")
+        self._s = h
+        self._keep = {}
+
+    def close(self):
+        if self._s is not None:
+            self._lib.sar_server_destroy(self._s)
+            self._s = None
+            self._keep = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, plan: "Plan", beat, q_tx, q_rx, w_az=None, image=None, M=None) -> int:
+        """Queue one frame; returns its ticket (raises SarError, e.g. SAR_EAGAIN)."""
+        M = beat.shape[0] if M is None else M
+        req = RequestDesc(plan=plan.handle.value, beat_host=_ptr(beat), M=M, w_az_host=_ptr(w_az),
+                          q_tx_host=_ptr(q_tx), q_rx_host=_ptr(q_rx), image_host=_ptr(image))
+        t = ctypes.c_uint64()
+        _check(self._lib.sar_submit(self._s, ctypes.byref(req), ctypes.byref(t)), "sar_submit")
+        self._keep[t.value] = (plan, beat, q_tx, q_rx, w_az, image)
+        return t.value
+
+    def poll(self, ticket: int):
+        """(status, state, device image pointer, latency_ms)."""
+        st, img, lat = ctypes.c_int32(), ctypes.c_void_p(), ctypes.c_double()
+        rc = self._lib.sar_poll(self._s, ticket, ctypes.byref(st), ctypes.byref(img),
+                                ctypes.byref(lat))
+        return rc, st.value, img.value, lat.value
+
+    def wait(self, ticket: int, timeout_ms: float = 60000.0) -> int:
+        return self._lib.sar_wait(self._s, ticket, timeout_ms)
+
+    def release(self, ticket: int) -> int:
+        rc = self._lib.sar_release(self._s, ticket)
+        self._keep.pop(ticket, None)
+        return rc
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        _check(self._lib.sar_server_get_stats(self._s, ctypes.byref(st)), "sar_server_get_stats")
+        return st

@@ -884,6 +884,57 @@ int sar_batch_launch(sar_batch *b, void *stream) {
                                                                                                  : SAR_ECUDA;
 }
 
+}  // extern "C"
+
+namespace sar {
+
+// Append a sub-aperture request whose profile samples (and FP16 scales) start
+// at the given rows; used by the server.  Same checks as sar_batch_add except
+// the 256-byte alignment of the profile block (rows keep their sample
+// alignment).
+int batch_add_rows(sar_batch *b, sar_plan *plan, const void *samples, const float *scales, int32_t M,
+                   const double *q_tx, const double *q_rx, void *image, int32_t accumulate) {
+    if (!b || !plan || !samples || (plan->fp16 && !scales)) return SAR_EINVAL;
+    if (b->n_jobs >= b->max_jobs || plan->device != b->device) return SAR_EINVAL;
+    if (!q_tx || !q_rx || !image || M < 1 || M > plan->p.max_pulses) return SAR_EINVAL;
+    if (b->upload_pending) {
+        if (cudaEventSynchronize(b->uploaded) != cudaSuccess) return SAR_ECUDA;
+        b->upload_pending = false;
+    }
+    BpArgs a;
+    size_t smem = 0;
+    // fill from a dummy aligned base, then point at the given rows
+    int rc = fill_bp_args(plan, (const void *)256, M, q_tx, q_rx, image, accumulate, &a, &smem);
+    if (rc) return rc;
+    a.prof = samples;
+    a.prof_scale = plan->fp16 ? scales : nullptr;
+    b->h_jobs[b->n_jobs] = a;
+    b->h_ub[b->n_jobs] = b->units;
+    b->h_tb[b->n_jobs] = b->tiles;
+    b->units += a.units;
+    b->tiles += a.n_tiles;
+    b->smem = std::max(b->smem, smem);
+    b->n_jobs += 1;
+    b->committed = false;
+    return SAR_OK;
+}
+
+int plan_geometry(const sar_plan *pl, int *n_rx, int *n_samples, int *n_bins, int *fp16, int64_t *n_pixels,
+                  int *max_pulses) {
+    if (!pl) return SAR_EINVAL;
+    *n_rx = pl->p.n_rx;
+    *n_samples = pl->p.n_samples;
+    *n_bins = pl->n_bins;
+    *fp16 = pl->fp16 ? 1 : 0;
+    *n_pixels = pl->n_pixels;
+    *max_pulses = pl->p.max_pulses;
+    return SAR_OK;
+}
+
+}  // namespace sar
+
+extern "C" {
+
 int sar_batch_get_info(const sar_batch *b, int32_t *n_jobs, int64_t *units, int32_t *ctas) {
     if (!b) return SAR_EINVAL;
     if (n_jobs) *n_jobs = b->n_jobs;

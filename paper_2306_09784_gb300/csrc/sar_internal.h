@@ -104,6 +104,14 @@ cudaError_t launch_backproject(const BpArgs &a, const BpLaunch &l, cudaStream_t 
 cudaError_t bp_batch_prepare(size_t smem, int *ctas_per_sm);
 cudaError_t launch_backproject_batch(const BpBatchArgs &b, int total_tiles, size_t smem, cudaStream_t s);
 
+// Used by the server (serve.cpp).
+int batch_add_rows(sar_batch *b, sar_plan *plan, const void *samples, const float *scales, int32_t M,
+                   const double *q_tx, const double *q_rx, void *image, int32_t accumulate);
+int plan_geometry(const sar_plan *pl, int *n_rx, int *n_samples, int *n_bins, int *fp16, int64_t *n_pixels,
+                  int *max_pulses);
+int fill_bp_args(const sar_plan *pl, const void *prof, int M, const double *q_tx, const double *q_rx,
+                 void *image, int accumulate, BpArgs *out, size_t *smem);
+
 // Used by sar_backproject_noalloc (noalloc.cu).
 int plan_device(const sar_plan *pl);
 int backproject_with_scratch(sar_plan *pl, const void *prof, int M, const double *q_tx, const double *q_rx,

@@ -83,6 +83,10 @@ int main(void) {
   P(sar_radar_params, kaiser_beta) P(sar_radar_params, phase_sign) P(sar_radar_params, max_doppler_bins)
   P(sar_grid, pixels_xy) P(sar_grid, n_pixels)
   P(sar_plan_info, n_pixels) P(sar_plan_info, bins_per_metre) P(sar_plan_info, device_bytes)
+  printf("sar_server_config %zu\nsar_request %zu\nsar_server_stats %zu\n",
+         sizeof(sar_server_config), sizeof(sar_request), sizeof(sar_server_stats));
+  P(sar_request, M) P(sar_request, w_az_host) P(sar_request, image_host)
+  P(sar_server_config, chunk_pulses) P(sar_server_stats, rounds) P(sar_server_stats, pool_bytes)
   return 0;
 }
 """
@@ -104,3 +108,12 @@ int main(void) {
     assert int(got["sar_plan_info.n_pixels"]) == sar.PlanInfo.n_pixels.offset
     assert int(got["sar_plan_info.bins_per_metre"]) == sar.PlanInfo.bins_per_metre.offset
     assert int(got["sar_plan_info.device_bytes"]) == sar.PlanInfo.device_bytes.offset
+    assert int(got["sar_server_config"]) == ctypes.sizeof(sar.ServerConfig)
+    assert int(got["sar_request"]) == ctypes.sizeof(sar.RequestDesc)
+    assert int(got["sar_server_stats"]) == ctypes.sizeof(sar.ServerStats)
+    assert int(got["sar_request.M"]) == sar.RequestDesc.M.offset
+    assert int(got["sar_request.w_az_host"]) == sar.RequestDesc.w_az_host.offset
+    assert int(got["sar_request.image_host"]) == sar.RequestDesc.image_host.offset
+    assert int(got["sar_server_config.chunk_pulses"]) == sar.ServerConfig.chunk_pulses.offset
+    assert int(got["sar_server_stats.rounds"]) == sar.ServerStats.rounds.offset
+    assert int(got["sar_server_stats.pool_bytes"]) == sar.ServerStats.pool_bytes.offset
