@@ -29,7 +29,7 @@ EXPORTS = (
     "sar_batch_create", "sar_batch_destroy", "sar_batch_clear", "sar_batch_add",
     "sar_batch_commit", "sar_batch_launch", "sar_batch_get_info",
     "sar_server_create", "sar_server_destroy", "sar_submit", "sar_poll", "sar_wait",
-    "sar_release", "sar_server_get_stats",
+    "sar_release", "sar_server_get_stats", "sar_plan_autotune",
 )
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 
@@ -130,6 +130,7 @@ def load_library(path: str = LIB_PATH):
     lib.sar_batch_get_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(i32)]
     lib.sar_plan_check_errors.argtypes = [vp]
+    lib.sar_plan_autotune.argtypes = [vp, vp, i32, vp, vp, vp, vp]
     lib.sar_status_string.argtypes = [ctypes.c_int]
     lib.sar_status_string.restype = ctypes.c_char_p
     lib.sar_version.argtypes = []
@@ -295,6 +296,15 @@ class Plan:
                                              _ptr(q_rx), _ptr(image), _stream(stream)),
                "sar_form_image_host")
         return image
+
+    def autotune(self, prof, M: int, q_tx, q_rx, image, stream=None):
+        """Pick the fastest backprojection launch shape on these inputs."""
+        _check(self._lib.sar_plan_autotune(self._plan, _ptr(prof), M, _ptr(q_tx), _ptr(q_rx),
+                                           _ptr(image), _stream(stream)), "sar_plan_autotune")
+        _check(self._lib.sar_plan_get_info(self._plan, ctypes.byref(self.info)),
+               "sar_plan_get_info")
+        return {"pulses_per_block": int(self.info.pulses_per_block),
+                "bp_ctas": int(self.info.bp_ctas)}
 
     def check_errors(self) -> int:
         return self._lib.sar_plan_check_errors(self._plan)

@@ -32,7 +32,8 @@ struct sar_plan {
     int n_tiles = 0;
     int L = 0, Mb = 0, rg = 1;
     size_t bp_smem = 0;
-    int num_sms = 0, ctas_per_sm = 0, G = 0, seg_cap = 0;
+    int num_sms = 0, ctas_per_sm = 0, G = 0, seg_cap = 0, minb = 2;
+    size_t partial_slots = 0;  // partial-sum tile slots allocated
     float fd_max = 0.f;
     // device memory owned by the plan
     float *d_wr = nullptr;
@@ -380,13 +381,18 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
     }
     pl->num_sms = prop.multiProcessorCount;
     if (bp_prepare(pl->fp16, pl->rg, pl->bp_smem) != cudaSuccess ||
-        bp_occupancy(pl->fp16, pl->rg, pl->bp_smem, &pl->ctas_per_sm) != 0 || pl->ctas_per_sm < 1) {
+        bp_occupancy(pl->fp16, pl->rg, pl->bp_smem, pl->minb, &pl->ctas_per_sm) != 0 || pl->ctas_per_sm < 1) {
         cudaGetLastError();
         delete pl;
         return SAR_ECUDA;
     }
     pl->G = pl->num_sms * pl->ctas_per_sm;
-    pl->seg_cap = pl->n_tiles / pl->G + 2;
+    // partial sums sized for any grid up to 3 CTAs per SM (the autotuner's range)
+    {
+        const int g_min = std::min(pl->G, pl->num_sms * 2), g_max = std::max(pl->G, pl->num_sms * 3);
+        pl->seg_cap = pl->n_tiles / g_min + 2;
+        pl->partial_slots = (size_t)g_max * pl->seg_cap;
+    }
 
     // FP64 tables
     std::vector<float> wr = range_window(p.range_window, p.n_samples, p.kaiser_beta);
@@ -412,7 +418,7 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
     if (!rc) rc = upload(pl, ht.tiles, &pl->d_tiles);
     if (!rc) {
         void *q = nullptr;
-        rc = dev_alloc(pl, (size_t)pl->G * pl->seg_cap * kTilePx * sizeof(float2), &q);
+        rc = dev_alloc(pl, pl->partial_slots * kTilePx * sizeof(float2), &q);
         pl->d_partial = (float2 *)q;
     }
     if (!rc) {
@@ -505,8 +511,8 @@ int bp_launch(sar_plan *pl, const void *prof, int M, const double *q_tx, const d
     const double cb = -pl->sign * 2.0 * kPi * (pl->beta - std::floor(pl->beta));
     a.cb = make_float2((float)std::cos(cb), (float)std::sin(cb));
     a.fd_max = pl->fd_max;
-    if ((long long)a.G * a.seg_max > (long long)pl->G * pl->seg_cap) return SAR_EINVAL;  // cannot happen
-    BpLaunch l{pl->rg, pl->fp16, pl->bp_smem};
+    if ((size_t)a.G * a.seg_max > pl->partial_slots) return SAR_EINVAL;  // cannot happen
+    BpLaunch l{pl->rg, pl->fp16, pl->bp_smem, pl->minb};
     DeviceGuard dg(pl->device);
     if (!dg.ok) return SAR_ECUDA;
     return launch_backproject(a, l, s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
@@ -620,7 +626,7 @@ int backproject_with_scratch(sar_plan *pl, const void *prof, int M, const double
     a.fd_max = pl->fd_max;
     const size_t need = (size_t)a.G * (size_t)a.seg_max * kTilePx * sizeof(float2);
     if (need > scratch_bytes) return SAR_ESCRATCH;
-    BpLaunch l{pl->rg, pl->fp16, pl->bp_smem};
+    BpLaunch l{pl->rg, pl->fp16, pl->bp_smem, pl->minb};
     DeviceGuard dg(pl->device);
     if (!dg.ok) return SAR_ECUDA;
     return launch_backproject(a, l, s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
@@ -941,6 +947,81 @@ int sar_batch_get_info(const sar_batch *b, int32_t *n_jobs, int64_t *units, int3
     if (units) *units = b->units;
     if (ctas) *ctas = b->G;
     return SAR_OK;
+}
+
+int sar_plan_autotune(sar_plan *pl, const void *prof_dev, int32_t M, const double *q_tx_dev,
+                      const double *q_rx_dev, void *image_dev, void *stream) {
+    if (!pl || !prof_dev || !q_tx_dev || !q_rx_dev || !image_dev || M < 1 || M > pl->p.max_pulses)
+        return SAR_EINVAL;
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return SAR_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    struct Cfg {
+        int minb, Mb, G;
+        size_t smem;
+    };
+    std::vector<Cfg> cands;
+    const size_t budgets[2] = {kBpSmemTarget, 73 * 1024};
+    for (int minb = 2; minb <= 3; ++minb) {
+        int mb_max = 0;
+        for (int mb = kMaxPulsesPerBlock; mb >= 1; --mb)
+            if (bp_smem_bytes(mb, pl->p.n_rx, pl->L, pl->fp16) <= budgets[minb - 2]) {
+                mb_max = mb;
+                break;
+            }
+        if (mb_max == 0) continue;
+        for (int mb : {mb_max, std::max(1, (mb_max * 2) / 3), std::max(1, mb_max / 2)}) {
+            const size_t smem = bp_smem_bytes(mb, pl->p.n_rx, pl->L, pl->fp16);
+            int occ = 0;
+            if (bp_occupancy(pl->fp16, pl->rg, smem, minb, &occ) != 0 || occ < 1) {
+                cudaGetLastError();
+                continue;
+            }
+            occ = std::min(occ, minb);
+            const Cfg c{minb, mb, pl->num_sms * occ, smem};
+            bool dup = false;
+            for (const Cfg &d : cands) dup |= (d.minb == c.minb && d.Mb == c.Mb);
+            if (!dup) cands.push_back(c);
+        }
+    }
+    if (cands.empty()) return SAR_EINVAL;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SAR_ECUDA;
+    const int save_minb = pl->minb, save_mb = pl->Mb, save_g = pl->G;
+    const size_t save_smem = pl->bp_smem;
+    float best = 1e30f;
+    Cfg best_c{save_minb, save_mb, save_g, save_smem};
+    int rc = SAR_OK;
+    for (const Cfg &c : cands) {
+        pl->minb = c.minb;
+        pl->Mb = c.Mb;
+        pl->G = c.G;
+        pl->bp_smem = c.smem;
+        float times[3];
+        for (int rep = -1; rep < 3 && rc == SAR_OK; ++rep) {
+            if (rep >= 0 && cudaEventRecord(e0, s) != cudaSuccess) rc = SAR_ECUDA;
+            if (!rc) rc = bp_launch(pl, prof_dev, M, q_tx_dev, q_rx_dev, nullptr, image_dev, 0, s);
+            if (!rc && rep >= 0) {
+                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&times[rep], e0, e1) != cudaSuccess)
+                    rc = SAR_ECUDA;
+            }
+        }
+        if (rc) break;
+        std::sort(times, times + 3);
+        if (times[1] < best) {
+            best = times[1];
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pl->minb = rc ? save_minb : best_c.minb;
+    pl->Mb = rc ? save_mb : best_c.Mb;
+    pl->G = rc ? save_g : best_c.G;
+    pl->bp_smem = rc ? save_smem : best_c.smem;
+    pl->ctas_per_sm = pl->G / pl->num_sms;
+    return rc;
 }
 
 int sar_plan_check_errors(sar_plan *pl) {

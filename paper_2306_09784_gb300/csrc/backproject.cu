@@ -52,8 +52,12 @@ constexpr double kExpansionTolBins = 2e-6;
 // Shared memory per CTA: two (A, D) table slots, one raw staging buffer and
 // three slots of per-pulse constants.
 struct Layout {
-    uint32_t table, raw, txr, txc, rxr, rxt, pair, total;
+    uint32_t table, raw, txr, txc, rxr, rxt, pair, flags, total;
 };
+
+// Per-block loop choice, OR-reduced over the CTA's FP64 tasks.
+constexpr int kFlagExact = 1;    // the expansion loop cannot take the block
+constexpr int kFlagOffAxis = 2;  // some Rx offset has a y component
 
 __host__ __device__ inline Layout bp_layout(int Mb, int R, int L, bool fp16) {
     Layout s;
@@ -73,6 +77,8 @@ __host__ __device__ inline Layout bp_layout(int Mb, int R, int L, bool fp16) {
     off += 3u * Mb * R * 16u;
     s.pair = off;  // int4 (idx0 bits, table address constant, k_lo, FP16 scale bits)
     off += 3u * Mb * R * 16u;
+    s.flags = off;  // int per constant slot: loop choice of the block (kFlag*)
+    off += 16u;
     s.total = off;
     return s;
 }
@@ -154,10 +160,17 @@ struct Smem {
         return reinterpret_cast<float4 *>(base + lay.rxt) + slot * MbR;
     }
     __device__ int4 *pair(int slot, int MbR) const { return reinterpret_cast<int4 *>(base + lay.pair) + slot * MbR; }
+    __device__ int *flags() const { return reinterpret_cast<int *>(base + lay.flags); }
     __device__ float4 *table(int slot, int MbRL) const {
         return reinterpret_cast<float4 *>(base + lay.table) + (size_t)slot * MbRL;
     }
 };
+
+// OR of the threads' flag bits into a shared slot (one atomic per warp).
+__device__ __forceinline__ void or_flags(int *slot, int bits) {
+    const int w = (int)__reduce_or_sync(0xffffffffu, (unsigned)bits);
+    if ((threadIdx.x & 31) == 0 && w) atomicOr(slot, w);
+}
 
 // FP64 stage for one pulse block into constant slot `cslot`, with the
 // table address constants pointing at table slot `tslot`: the Tx records of
@@ -193,7 +206,7 @@ __device__ __forceinline__ int prep_block(const BpArgs &a, const Smem &sm, const
                     (int)floor(a.a1 * (2.0 * r_tx - 2.0 * ti.rho - o_allow) - (double)a.fd_max) - kGuardBins;
                 c = make_int4(__float_as_int((float)(2.0 * a.a1 * r_tx - (double)k_lo)), k_lo, 0, 0);
             } else {
-                exact = 1;
+                exact = kFlagExact;
             }
             txr[p] = t4;
             txc[p] = c;
@@ -216,7 +229,10 @@ __device__ __forceinline__ int prep_block(const BpArgs &a, const Smem &sm, const
             const double o2 = ox * ox + oy * oy;
             const double cexp = 0.5 * o2 - (wx * ox + wy * oy);
             const uint32_t addr_c = table_addr + (uint32_t)(task * a.L) * 16u - kMagicBits * 16u;
-            rxt[task] = make_float4((float)-ox, (float)-oy, (float)cexp, __uint_as_float(addr_c));
+            // halved so that the pixel loop gets a / 2 directly
+            rxt[task] = make_float4((float)(-0.5 * ox), (float)(-0.5 * oy), (float)(0.5 * cexp),
+                                    __uint_as_float(addr_c));
+            if (!(fabs(oy) <= 1e-9)) exact |= kFlagOffAxis;
             const float scale = a.prof_scale ? __ldg(a.prof_scale + (long long)m * R + r) : 1.0f;
             pr[task].w = __float_as_int(scale);
             // path criteria (FP32 is plenty; non-finite input fails them)
@@ -225,7 +241,7 @@ __device__ __forceinline__ int prep_block(const BpArgs &a, const Smem &sm, const
             const float dmin = rt - rho;
             const bool expand = rt > 2.0f * rho + oa + 1e-3f && rt < (float)kMaxRange &&
                                 oa <= (float)o_allow && (float)o2 * oa <= tol2 * dmin * dmin;
-            exact |= expand ? 0 : 1;
+            exact |= expand ? 0 : kFlagExact;
         }
     }
     return exact;
@@ -374,7 +390,7 @@ __device__ __forceinline__ void accumulate(float idx, uint32_t ac, float k2pb, f
 // PU consecutive pulses of the expansion loop, unrolled together so that
 // RG x PU x 4 updates per thread are independent (latency hiding for small
 // Rx counts).
-template <int RG, int PU, bool FD>
+template <int RG, int PU, bool FD, bool AXIS>
 __device__ __forceinline__ void expand_pulses(const BpArgs &a, const float4 *txr, const int4 *txc,
                                               const float4 *rxt, int p,
                                               const float (&dx)[kPxPerThread],
@@ -384,7 +400,7 @@ __device__ __forceinline__ void expand_pulses(const BpArgs &a, const float4 *txr
                                               float (&acc_re)[kPxPerThread],
                                               float (&acc_im)[kPxPerThread]) {
     const int R = a.R;
-    const float a1 = a.a1f, two_a1 = 2.0f * a.a1f, half_a1 = 0.5f * a.a1f;
+    const float two_a1 = 2.0f * a.a1f;
     const float k2pb = a.two_pi_beta;
     float u[PU][kPxPerThread], ay[PU][kPxPerThread], kk[PU][kPxPerThread];
 #pragma unroll
@@ -395,11 +411,11 @@ __device__ __forceinline__ void expand_pulses(const BpArgs &a, const float4 *txr
         for (int j = 0; j < kPxPerThread; ++j) {
             float y;
             const float dt = range_delta(t4, dx[j], dy[j], hd2[j], y);
-            // index of the Tx part (twice the Tx range) and the expansion
-            // coefficients a1/d and a1/(2 d^3)
+            // index of the Tx part (twice the Tx range) and, with w = a / 2,
+            // a1 (d_rx - d_tx) = w (2 a1 / d - w 2 a1 / d^3)
             u[q][j] = fmaf(two_a1, dt, FD ? cidx + fdi[j] : cidx);
-            ay[q][j] = a1 * y;
-            kk[q][j] = (half_a1 * y) * (y * y);
+            ay[q][j] = two_a1 * y;
+            kk[q][j] = ay[q][j] * (y * y);
         }
     }
     for (int r0 = 0; r0 < R; r0 += RG) {
@@ -411,10 +427,10 @@ __device__ __forceinline__ void expand_pulses(const BpArgs &a, const float4 *txr
                 const uint32_t ac = __float_as_uint(o4.w);
 #pragma unroll
                 for (int j = 0; j < kPxPerThread; ++j) {
-                    // a = |o|^2/2 - (p - q_tx).o;  a1 (d_rx - d_tx) = a (a1/d - a a1/(2 d^3))
-                    const float av = fmaf(o4.x, dx[j], fmaf(o4.y, dy[j], o4.z));
-                    const float m1 = fmaf(-av, kk[q][j], ay[q][j]);
-                    const float idx = fmaf(av, m1, u[q][j]);
+                    // w = a / 2 = (|o|^2/2 - (p - q_tx).o) / 2 (rxt holds halved constants)
+                    const float w = AXIS ? fmaf(o4.x, dx[j], o4.z) : fmaf(o4.x, dx[j], fmaf(o4.y, dy[j], o4.z));
+                    const float m1 = fmaf(-w, kk[q][j], ay[q][j]);
+                    const float idx = fmaf(w, m1, u[q][j]);
                     accumulate(idx, ac, k2pb, acc_re[j], acc_im[j]);
                 }
             }
@@ -425,7 +441,7 @@ __device__ __forceinline__ void expand_pulses(const BpArgs &a, const float4 *txr
 // Expansion loop over one pulse block (far field, small Rx offsets).  When
 // all Rx channels of a pulse fit one group (R == RG < 3), 4 / RG pulses are
 // processed together; the per-pixel summation order stays pulse by pulse.
-template <int RG, bool FD>
+template <int RG, bool FD, bool AXIS>
 __device__ __forceinline__ void compute_block_expand(const BpArgs &a, const Smem &sm, int b, int cslot,
                                                      const float (&dx)[kPxPerThread],
                                                      const float (&dy)[kPxPerThread],
@@ -442,9 +458,10 @@ __device__ __forceinline__ void compute_block_expand(const BpArgs &a, const Smem
     int p = 0;
     if (PU > 1 && R == RG) {
         for (; p + PU <= np; p += PU)
-            expand_pulses<RG, PU, FD>(a, txr, txc, rxt, p, dx, dy, hd2, fdi, acc_re, acc_im);
+            expand_pulses<RG, PU, FD, AXIS>(a, txr, txc, rxt, p, dx, dy, hd2, fdi, acc_re, acc_im);
     }
-    for (; p < np; ++p) expand_pulses<RG, 1, FD>(a, txr, txc, rxt, p, dx, dy, hd2, fdi, acc_re, acc_im);
+    for (; p < np; ++p)
+        expand_pulses<RG, 1, FD, AXIS>(a, txr, txc, rxt, p, dx, dy, hd2, fdi, acc_re, acc_im);
 }
 
 // Exact loop over one pulse block: every distance from its own rsqrt and
@@ -521,41 +538,49 @@ __device__ __forceinline__ void process_segment(const BpArgs &a, const Smem &sm,
         acc_im[j] = 0.f;
     }
 
-    // pipeline prologue; the loop choices (exact or expansion) of blocks
-    // b, b+1, b+2 are block-uniform (reduced by the barriers)
-    int fl = prep_block(a, sm, ti, b0, 0, 0);
-    if (b0 + 1 < b1) fl |= prep_block(a, sm, ti, b0 + 1, 1, 1) << 1;
-    int ex_cur = __syncthreads_or(fl & 1);
-    int ex_next = __syncthreads_or(fl & 2) ? 1 : 0;
-    if (ex_cur) {
+    // pipeline prologue.  The loop choice of each block (kFlag* bits) is
+    // OR-reduced into a shared slot per constant slot and read after the
+    // next barrier; slot j is cleared at the end of the iteration that
+    // computes its block, before the block three ahead reuses it.
+    int *bfl = sm.flags();
+    if (threadIdx.x < 3) bfl[threadIdx.x] = 0;
+    __syncthreads();
+    or_flags(bfl + 0, prep_block(a, sm, ti, b0, 0, 0));
+    if (b0 + 1 < b1) or_flags(bfl + 1, prep_block(a, sm, ti, b0 + 1, 1, 1));
+    __syncthreads();
+    int f_cur = bfl[0];
+    int f_next = (b0 + 1 < b1) ? bfl[1] : 0;
+    if (f_cur & kFlagExact) {
         prep_exact(a, sm, ti, b0, 0, 0);
         __syncthreads();
     }
-    stage_block<FP16>(a, sm, b0, 0, ex_cur);
+    stage_block<FP16>(a, sm, b0, 0, f_cur & kFlagExact);
     cp_async_commit();
     cp_async_wait_all();
-    convert_block<FP16>(a, sm, b0, 0, 0, ex_cur);
+    convert_block<FP16>(a, sm, b0, 0, 0, f_cur & kFlagExact);
     __syncthreads();
 
     for (int b = b0; b < b1; ++b) {
         const int k = b - b0;
-        int ex_new = 0;
-        if (b + 2 < b1) ex_new = prep_block(a, sm, ti, b + 2, (k + 2) % 3, (k + 2) & 1);
-        if (b + 1 < b1 && ex_next) {  // block-uniform
+        if (b + 2 < b1) or_flags(bfl + (k + 2) % 3, prep_block(a, sm, ti, b + 2, (k + 2) % 3, (k + 2) & 1));
+        if (b + 1 < b1 && (f_next & kFlagExact)) {  // block-uniform
             prep_exact(a, sm, ti, b + 1, (k + 1) % 3, (k + 1) & 1);
             __syncthreads();
         }
-        if (b + 1 < b1) stage_block<FP16>(a, sm, b + 1, (k + 1) % 3, ex_next);
+        if (b + 1 < b1) stage_block<FP16>(a, sm, b + 1, (k + 1) % 3, f_next & kFlagExact);
         cp_async_commit();
-        if (ex_cur)
+        if (f_cur & kFlagExact)
             compute_block_exact<RG, FD>(a, sm, b, k % 3, dx, dy, hd2, fdi, acc_re, acc_im);
+        else if (f_cur & kFlagOffAxis)
+            compute_block_expand<RG, FD, false>(a, sm, b, k % 3, dx, dy, hd2, fdi, acc_re, acc_im);
         else
-            compute_block_expand<RG, FD>(a, sm, b, k % 3, dx, dy, hd2, fdi, acc_re, acc_im);
+            compute_block_expand<RG, FD, true>(a, sm, b, k % 3, dx, dy, hd2, fdi, acc_re, acc_im);
         cp_async_wait_all();
-        if (b + 1 < b1) convert_block<FP16>(a, sm, b + 1, (k + 1) % 3, (k + 1) & 1, ex_next);
-        ex_new = __syncthreads_or(ex_new);
-        ex_cur = ex_next;
-        ex_next = ex_new;
+        if (b + 1 < b1) convert_block<FP16>(a, sm, b + 1, (k + 1) % 3, (k + 1) & 1, f_next & kFlagExact);
+        if (threadIdx.x == 0) bfl[k % 3] = 0;  // block b's slot, free for block b + 3
+        __syncthreads();
+        f_cur = f_next;
+        f_next = (b + 2 < b1) ? bfl[(k + 2) % 3] : 0;
     }
 
     if (FD) {
@@ -593,8 +618,10 @@ __device__ __forceinline__ void process_segment(const BpArgs &a, const Smem &sm,
     }
 }
 
-template <int RG, bool FP16, bool FD>
-__global__ void __launch_bounds__(kBpThreads, 2) backproject_kernel(BpArgs a) {
+// MINB: CTAs per SM the register budget is sized for (2: 128 registers and
+// more independent updates per thread; 3: 80 registers and more warps).
+template <int RG, bool FP16, bool FD, int MINB>
+__global__ void __launch_bounds__(kBpThreads, MINB) backproject_kernel(BpArgs a) {
     extern __shared__ __align__(16) unsigned char smem_bp[];
     Smem sm;
     sm.base = smem_bp;
@@ -731,15 +758,15 @@ __global__ void __launch_bounds__(256) bp_fixup_kernel(BpArgs a) {
 }
 
 template <int RG, bool FP16, bool FD>
-void *kernel_ptr() {
-    return (void *)backproject_kernel<RG, FP16, FD>;
+void *kernel_ptr(int minb) {
+    return minb == 3 ? (void *)backproject_kernel<RG, FP16, FD, 3> : (void *)backproject_kernel<RG, FP16, FD, 2>;
 }
 
-void *select_kernel(int rg, bool fp16, bool fd) {
-#define SAR_SEL(RGV)                                                                          \
-    if (rg == RGV) {                                                                          \
-        if (fp16) return fd ? kernel_ptr<RGV, true, true>() : kernel_ptr<RGV, true, false>(); \
-        return fd ? kernel_ptr<RGV, false, true>() : kernel_ptr<RGV, false, false>();         \
+void *select_kernel(int rg, bool fp16, bool fd, int minb) {
+#define SAR_SEL(RGV)                                                                                    \
+    if (rg == RGV) {                                                                                    \
+        if (fp16) return fd ? kernel_ptr<RGV, true, true>(minb) : kernel_ptr<RGV, true, false>(minb); \
+        return fd ? kernel_ptr<RGV, false, true>(minb) : kernel_ptr<RGV, false, false>(minb);         \
     }
     SAR_SEL(1)
     SAR_SEL(2)
@@ -760,17 +787,18 @@ constexpr int kSmemLimit = 227 * 1024;
 
 cudaError_t bp_prepare(bool fp16, int rg, size_t smem) {
     if (smem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
-    for (int fd = 0; fd < 2; ++fd) {
-        void *k = select_kernel(rg, fp16, fd != 0);
-        if (!k) return cudaErrorInvalidValue;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
-        if (e != cudaSuccess) return e;
-    }
+    for (int fd = 0; fd < 2; ++fd)
+        for (int minb = 2; minb <= 3; ++minb) {
+            void *k = select_kernel(rg, fp16, fd != 0, minb);
+            if (!k) return cudaErrorInvalidValue;
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+            if (e != cudaSuccess) return e;
+        }
     return cudaSuccess;
 }
 
-int bp_occupancy(bool fp16, int rg, size_t smem, int *ctas_per_sm) {
-    void *k = select_kernel(rg, fp16, false);
+int bp_occupancy(bool fp16, int rg, size_t smem, int minb, int *ctas_per_sm) {
+    void *k = select_kernel(rg, fp16, false, minb);
     if (!k) return -1;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kBpThreads, smem) != cudaSuccess) return -1;
@@ -796,7 +824,7 @@ cudaError_t launch_backproject_batch(const BpBatchArgs &b, int total_tiles, size
 }
 
 cudaError_t launch_backproject(const BpArgs &a, const BpLaunch &l, cudaStream_t s) {
-    void *k = select_kernel(l.rg, l.fp16, a.fdopp != nullptr);
+    void *k = select_kernel(l.rg, l.fp16, a.fdopp != nullptr, l.minb);
     if (!k) return cudaErrorInvalidValue;
     if (a.units == 0) return cudaSuccess;
     BpArgs args = a;

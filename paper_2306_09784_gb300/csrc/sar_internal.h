@@ -95,11 +95,12 @@ struct BpLaunch {
     int rg;       // Rx group size of the inner loop (1, 2, 3 or 4)
     bool fp16;
     size_t smem;  // dynamic shared memory bytes
+    int minb;     // CTAs per SM the kernel's registers are sized for (2 or 3)
 };
 
 size_t bp_smem_bytes(int Mb, int R, int L, bool fp16);
 cudaError_t bp_prepare(bool fp16, int rg, size_t smem);  // sets function attributes
-int bp_occupancy(bool fp16, int rg, size_t smem, int *ctas_per_sm);
+int bp_occupancy(bool fp16, int rg, size_t smem, int minb, int *ctas_per_sm);
 cudaError_t launch_backproject(const BpArgs &a, const BpLaunch &l, cudaStream_t s);
 cudaError_t bp_batch_prepare(size_t smem, int *ctas_per_sm);
 cudaError_t launch_backproject_batch(const BpBatchArgs &b, int total_tiles, size_t smem, cudaStream_t s);

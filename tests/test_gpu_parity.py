@@ -426,3 +426,42 @@ def test_precision_config_sampled(torch, precision):
     assert err <= (TOL_FP32 if precision == 0 else TOL_FP16), err
     bad = check_peaks(img[idx], ref_s, [np.array([pos[int(i)] for i in w]) for w in wins])
     assert bad == []
+
+
+def test_autotune_keeps_results(torch, small):
+    """The autotuner changes only the launch shape: the image stays within
+    FP32 summation order of the default shape and within tolerance of the
+    oracle."""
+    wl, beat, w_az = small
+    plan = make_plan(wl, precision=1)
+    before = gpu_image(plan, wl, beat, w_az)
+    b, w, qt, qr = to_dev(wl, beat, w_az)
+    prof = plan.range_compress(b, w)
+    scratch = torch.zeros(plan.n_pixels, dtype=torch.complex64, device="cuda")
+    shape = plan.autotune(prof, wl.n_pulses, qt, qr, scratch)
+    assert shape["pulses_per_block"] >= 1 and shape["bp_ctas"] >= 1
+    after = gpu_image(plan, wl, beat, w_az)
+    assert rel_l2(after, before) < 1e-5
+    assert rel_l2(after, oracle_image(wl, beat, w_az)) <= TOL_FP16
+
+
+def test_off_axis_rx_array(torch):
+    """Rx array tilted 30 degrees off the driving direction: the expansion
+    loop takes its general (x and y offset) form."""
+    radar = synth.Radar(n_samples=128, n_rx=4, os=4)
+    M = 64
+    rng = np.random.Generator(np.random.PCG64(31))
+    q_tx, _ = synth.trajectory(radar, M, jitter=0.01, rng=rng)
+    ang = np.deg2rad(30.0)
+    step = radar.wavelength / 2 * np.array([np.cos(ang), np.sin(ang)])
+    q_rx = q_tx[:, None, :] + (np.arange(4) + 1.0)[None, :, None] * step[None, None, :]
+    grid = synth.Grid(-0.9, 2.2, 0.04, 0.04, 45, 38)
+    tg = np.stack([rng.uniform(-0.8, 0.8, 6), rng.uniform(2.3, 3.6, 6)], 1)
+    am = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+    wl = synth.Workload("offaxis", radar, M, grid, q_tx, q_rx, tg, am, 20.0, 3,
+                        synth.crop_for(radar, grid, q_tx, q_rx))
+    beat = synth.workload_beat(wl)
+    w_az = np.hanning(M)
+    img = gpu_image(make_plan(wl), wl, beat, w_az)
+    ref = oracle_image(wl, beat, w_az)
+    assert rel_l2(img, ref) <= TOL_FP32
