@@ -15,6 +15,8 @@
 // rotation into the profile (see sar.h) and writes only the cropped bins.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "sar_internal.h"
 
 namespace sar {
@@ -101,7 +103,8 @@ __device__ __forceinline__ void dft_reg(float2 *v) {
 // (Ns = product of the radices of the earlier passes).  Each of the T = n/16
 // threads of the row owns 16 values: 16/RAD butterflies j = tid + g T.
 // FIRST: the pass reads the windowed beat samples from global memory.
-template <int RAD, int SGN, bool FIRST>
+// STAGED: the beat row, the window and the twiddles are in shared memory.
+template <int RAD, int SGN, bool FIRST, bool STAGED = false>
 __device__ __forceinline__ void stockham_pass(float2 *X, int n, int log2n, int Ns, int tid, int T,
                                               bool active, const float2 *__restrict__ tw,
                                               const float2 *__restrict__ beat_row,
@@ -118,8 +121,8 @@ __device__ __forceinline__ void stockham_pass(float2 *X, int n, int log2n, int N
             if (FIRST) {
                 float2 x = make_float2(0.f, 0.f);
                 if (active && idx < N) {
-                    const float2 b = __ldg(beat_row + idx);
-                    const float w = __ldg(w_r + idx);
+                    const float2 b = STAGED ? beat_row[idx] : __ldg(beat_row + idx);
+                    const float w = STAGED ? w_r[idx] : __ldg(w_r + idx);
                     x = make_float2(w * b.x, w * b.y);
                 }
                 v[g * RAD + r] = x;
@@ -136,10 +139,26 @@ __device__ __forceinline__ void stockham_pass(float2 *X, int n, int log2n, int N
         const int j = tid + g * T;
         const int k = j & (Ns - 1);
         if (Ns > 1) {
-#pragma unroll
-            for (int r = 1; r < RAD; ++r) {
-                v[g * RAD + r] = cmul(v[g * RAD + r], __ldg(tw + ((k * r) << tw_shift)));
+            // w^r for r < RAD from the loaded powers w, w^2, w^4, w^8 (at most
+            // three complex products deep: ~4e-7 relative error)
+            float2 wp[16];
+            const int t1 = k << tw_shift;
+            wp[1] = STAGED ? tw[t1] : __ldg(tw + t1);
+            if (RAD > 2) wp[2] = STAGED ? tw[2 * t1] : __ldg(tw + 2 * t1);
+            if (RAD > 4) wp[4] = STAGED ? tw[4 * t1] : __ldg(tw + 4 * t1);
+            if (RAD > 8) wp[8] = STAGED ? tw[8 * t1] : __ldg(tw + 8 * t1);
+            if (RAD > 2) wp[3] = cmul(wp[1], wp[2]);
+            if (RAD > 4) {
+                wp[5] = cmul(wp[4], wp[1]);
+                wp[6] = cmul(wp[4], wp[2]);
+                wp[7] = cmul(wp[4], wp[3]);
             }
+            if (RAD > 8) {
+#pragma unroll
+                for (int r = 9; r < 16; ++r) wp[r] = cmul(wp[8], wp[r - 8]);
+            }
+#pragma unroll
+            for (int r = 1; r < RAD; ++r) v[g * RAD + r] = cmul(v[g * RAD + r], wp[r]);
         }
         dft_reg<RAD, SGN>(v + g * RAD);
         const int base = (j - k) * RAD + k;
@@ -222,15 +241,156 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, BIG ? 1 : 3) range_compress_
     }
 }
 
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+// Output stage shared by both kernels: spectrum, FP32 profile or FP16
+// profile (scale = row max / 2^14) of the row held in X.
+template <int MODE>
+__device__ __forceinline__ void store_row(const RcArgs &a, const float2 *X, long long row, bool active, int tid,
+                                          int T, int lrow, int *row_max) {
+    const int n = a.n_fft;
+    if (MODE == kRcSpectrum) {
+        if (!active) return;
+        float2 *out = reinterpret_cast<float2 *>(a.out) + row * (long long)n;
+        for (int k = tid; k < n; k += T) out[k] = X[pad16(k)];
+        return;
+    }
+    const float g = (a.w_az != nullptr && active) ? __ldg(a.w_az + row / a.R) : 1.f;
+    if (MODE == kRcProfileF32) {
+        if (!active) return;
+        float2 *out = reinterpret_cast<float2 *>(a.out) + row * (long long)a.n_bins;
+        for (int i = tid; i < a.n_bins; i += T) {
+            const float2 v = cmul(X[pad16(a.crop_lo + i)], __ldg(a.rot + i));
+            out[i] = make_float2(g * v.x, g * v.y);
+        }
+        return;
+    }
+    float mx = 0.f;
+    if (active) {
+        for (int i = tid; i < a.n_bins; i += T) {
+            const float2 v = cmul(X[pad16(a.crop_lo + i)], __ldg(a.rot + i));
+            mx = fmaxf(mx, fmaxf(fabsf(g * v.x), fabsf(g * v.y)));
+        }
+    }
+    atomicMax(&row_max[lrow], __float_as_int(mx));
+    __syncthreads();
+    if (!active) return;
+    const float rmax = __int_as_float(row_max[lrow]);
+    const float scale = rmax > 0.f ? rmax * (1.0f / 16384.0f) : 1.0f;
+    const float inv = 1.0f / scale;
+    if (tid == 0) a.scales[row] = scale;
+    __half2 *out = reinterpret_cast<__half2 *>(a.out) + row * (long long)a.n_bins;
+    for (int i = tid; i < a.n_bins; i += T) {
+        const float2 v = cmul(X[pad16(a.crop_lo + i)], __ldg(a.rot + i));
+        out[i] = __floats2half2_rn(g * v.x * inv, g * v.y * inv);
+    }
+}
+
+// Persistent form for N_fft <= 4096 (256 threads, 4096 / N_fft rows per
+// group).  Twiddles and window sit in shared memory for the CTA's lifetime;
+// the beat samples of the next row group are copied in with cp.async while
+// the current group is transformed.
+template <int SGN, int MODE>
+__global__ void __launch_bounds__(256, 2) range_compress_persistent(RcArgs a, long long n_groups) {
+    extern __shared__ float2 smem_rcp[];
+    __shared__ int row_max[64];
+    const int n = a.n_fft, N = a.N;
+    const int T = n >> 4;
+    const int rows_per = blockDim.x / T;
+    const int lrow = threadIdx.x / T;
+    const int tid = threadIdx.x - lrow * T;
+    float2 *X = smem_rcp + (size_t)lrow * (n + n / 16);
+    float2 *tw = smem_rcp + (size_t)rows_per * (n + n / 16);
+    float2 *stage = tw + n;  // [2][rows_per][N]
+    float *wr = reinterpret_cast<float *>(stage + 2 * rows_per * N);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = __ldg(a.tw + i);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) wr[i] = __ldg(a.w_r + i);
+    const uint32_t stage_addr = (uint32_t)__cvta_generic_to_shared(stage);
+    const int per_group = rows_per * N;
+
+    auto issue = [&](long long g, int buf) {
+        for (int i = threadIdx.x; i < per_group; i += blockDim.x) {
+            const int lr = i / N;
+            const int k = i - lr * N;
+            const long long row = g * rows_per + lr;
+            const bool ok = row < a.rows;
+            const void *src = ok ? (const void *)(a.beat + row * (long long)N + k) : (const void *)a.beat;
+            cp_async8(stage_addr + (uint32_t)(buf * per_group + i) * 8u, src, ok ? 8u : 0u);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
+    long long g = blockIdx.x;
+    if (g < n_groups) issue(g, 0);
+    for (int it = 0; g < n_groups; g += gridDim.x, ++it) {
+        const long long gn = g + gridDim.x;
+        if (gn < n_groups) {
+            issue(gn, (it + 1) & 1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        if (MODE == kRcProfileF16 && threadIdx.x < 64) row_max[threadIdx.x] = 0;
+        __syncthreads();  // staged samples, twiddles and window visible
+        const long long row = g * rows_per + lrow;
+        const bool active = row < a.rows;
+        const float2 *src = stage + (size_t)((it & 1) * rows_per + lrow) * N;
+        const int n16 = a.log2n >> 2;
+        const int rem = a.log2n & 3;
+        int Ns = 1;
+        for (int p = 0; p < n16; ++p) {
+            if (p == 0)
+                stockham_pass<16, SGN, true, true>(X, n, a.log2n, Ns, tid, T, active, tw, src, wr, N);
+            else
+                stockham_pass<16, SGN, false, true>(X, n, a.log2n, Ns, tid, T, active, tw, src, wr, N);
+            Ns <<= 4;
+        }
+        if (rem == 1) stockham_pass<2, SGN, false, true>(X, n, a.log2n, Ns, tid, T, active, tw, src, wr, N);
+        if (rem == 2) stockham_pass<4, SGN, false, true>(X, n, a.log2n, Ns, tid, T, active, tw, src, wr, N);
+        if (rem == 3) stockham_pass<8, SGN, false, true>(X, n, a.log2n, Ns, tid, T, active, tw, src, wr, N);
+        store_row<MODE>(a, X, row, active, tid, T, lrow, row_max);
+        __syncthreads();  // X and this group's stage buffer are reused next
+    }
+}
+
 template <int SGN, int MODE>
 cudaError_t launch_rc(const RcArgs &a, cudaStream_t s) {
     const int n = a.n_fft;
+    if (n <= 4096) {
+        const int rows_per = 4096 / n;
+        const long long n_groups = (a.rows + rows_per - 1) / rows_per;
+        if (n_groups == 0) return cudaSuccess;
+        const size_t smem = ((size_t)rows_per * (n + n / 16) + n + 2 * (size_t)rows_per * a.N) * sizeof(float2) +
+                            (size_t)a.N * sizeof(float);
+        auto kern = range_compress_persistent<SGN, MODE>;
+        int dev = 0, sms = 0, optin = 0, occ = 0;
+        cudaFuncAttributes fa;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, kern) != cudaSuccess)
+            return cudaErrorInvalidConfiguration;
+        // process-wide attribute: the largest dynamic size the device allows
+        // next to the kernel's static shared memory
+        const int max_dyn = optin - (int)fa.sharedSizeBytes;
+        if ((int)smem > max_dyn) return cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn);
+        if (e != cudaSuccess) return e;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem) != cudaSuccess || occ < 1)
+            return cudaErrorInvalidConfiguration;
+        const long long grid = std::min<long long>(n_groups, (long long)sms * occ);
+        kern<<<(unsigned)grid, 256, smem, s>>>(a, n_groups);
+        return cudaGetLastError();
+    }
     const int T = n / 16;
     const int rows_per_cta = n >= 4096 ? 1 : 4096 / n;
     const int threads = T * rows_per_cta;
     const size_t smem = (size_t)rows_per_cta * (n + n / 16) * sizeof(float2);
     auto kern = n > 4096 ? range_compress_kernel<SGN, MODE, true> : range_compress_kernel<SGN, MODE, false>;
-    // process-wide attribute shared by all plans: set to the largest row size
+    // process-wide attribute shared by all plans: the largest row size
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(16384 * 17 / 16 * sizeof(float2)));
     if (e != cudaSuccess) return e;
