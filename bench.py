@@ -53,7 +53,7 @@ MUFU_LANES = 16
 # backprojection launch on this workload, from an ncu --set full capture of
 # the kernel source with this SHA-256 prefix (reported as null once the
 # kernel source differs).
-BP_TRAFFIC = {"sha256_16": "38da01bdbf0ff104", "bytes": 33753088 + 7424}
+BP_TRAFFIC = {"sha256_16": "16da3cfa7c70ee5e", "bytes": 33762560 + 9472}
 HBM_PEAK_FALLBACK_GBS = 6800.0
 
 
@@ -77,6 +77,24 @@ def hbm_peak_gbs():
 def alu_peak_updates(sm_mhz: float) -> float:
     hz = sm_mhz * 1e6
     return min(SMS * FP32_LANES * hz / ALG_FP32_OPS, SMS * MUFU_LANES * hz / ALG_MUFU_OPS)
+
+
+def max_over_ranks(seconds: float, ws: int, device=None) -> float:
+    """Slowest rank's timed-region length (a timing reduction, not a data-path
+    collective)."""
+    if ws <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(updates_per_frame: int, steps: int, ws: int, seconds: float) -> float:
+    """Whole-job G updates/s: every rank images its own frame each step
+    (weak scaling), divided by the slowest rank's time."""
+    return ws * updates_per_frame * steps / seconds / 1e9
 
 
 def dist_env():
@@ -491,12 +509,8 @@ def run_ours(args):
     step_ms = [e[0].elapsed_time(e[2]) for e in events]
     rc_ms = [e[0].elapsed_time(e[1]) for e in events]
     bp_ms = [e[1].elapsed_time(e[2]) for e in events]
-    total_s = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = ws * upd * args.steps / total_s / 1e9
+    total_s = max_over_ranks(sum(step_ms) / 1e3, ws, dev)
+    value = aggregate_rate(upd, args.steps, ws, total_s)
 
     # end to end through the host entry point: pinned host inputs, copies inside
     hb = torch.from_numpy(beat_np).pin_memory()

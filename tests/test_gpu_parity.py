@@ -465,3 +465,26 @@ def test_off_axis_rx_array(torch):
     img = gpu_image(make_plan(wl), wl, beat, w_az)
     ref = oracle_image(wl, beat, w_az)
     assert rel_l2(img, ref) <= TOL_FP32
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_kaiser_range_window(torch, small, precision):
+    """Kaiser range window (beta 6) instead of Hann (Sec. III-B)."""
+    import paper_2306_09784_gb300 as sar
+    wl, beat, w_az = small
+    plan = make_plan(wl, precision=precision, range_window=sar.WINDOW_KAISER, kaiser_beta=6.0)
+    img = gpu_image(plan, wl, beat, w_az)
+    ref = oracle_image(wl, beat, w_az, range_window=oracle.WINDOW_KAISER)
+    assert rel_l2(img, ref) <= (TOL_FP32 if precision == 0 else TOL_FP16)
+
+
+def test_fp16_doppler_conjugate(torch, small):
+    """FP16 profiles with Doppler offsets under the conjugate convention."""
+    wl, beat, w_az = small
+    rng = np.random.Generator(np.random.PCG64(8))
+    fd = rng.uniform(-1.0, 1.0, wl.grid.nx * wl.grid.ny)
+    bc = np.conj(beat).astype(np.complex64)
+    plan = make_plan(wl, precision=1, phase_sign=-1, max_doppler_bins=1.5)
+    img = gpu_image(plan, wl, bc, w_az, fdopp=fd)
+    ref = oracle_image(wl, bc, w_az, sign=-1, fd_idx=fd.astype(np.float32).astype(np.float64))
+    assert rel_l2(img, ref) <= TOL_FP16
