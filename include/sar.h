@@ -72,6 +72,10 @@ enum sar_precision {
  *  max_doppler_bins  bound on |f_doppler(p)| (in bins) of the Doppler
  *              offsets passed to sar_backproject; the staged bin windows are
  *              widened by it.  Offsets beyond the bound are clamped to it.
+ * The derived phase rate beta = f0 / (c a1) cycles per bin, a1 = slope N_fft
+ * / (c fs) bins per metre, must lie in [1e-9, 1e9] (f0 / (B os) for a chirp
+ * of bandwidth B; about 19 at 77 GHz, 1 GHz, os 4); sar_plan_create rejects
+ * other parameters with SAR_EINVAL.
  */
 typedef struct sar_radar_params {
     double f0;
@@ -123,6 +127,8 @@ typedef struct sar_plan_info {
     double bins_per_metre;      /* a1 = mu N_fft / (c fs) */
     double cycles_per_bin;      /* f0 / (c a1) */
     size_t device_bytes;        /* device memory the plan owns */
+    int32_t rx_group;           /* Rx channels per inner-loop group of the launch shape */
+    int32_t regs_ctas_per_sm;   /* CTAs per SM the launch's registers are sized for */
 } sar_plan_info;
 
 /*
@@ -331,9 +337,13 @@ int sar_server_get_stats(sar_server *server, sar_server_stats *stats);
 /*
  * Whole frame from host memory: copy beat, w_sar and trajectory to the
  * plan's device staging buffers, range-compress, backproject and copy the
- * image back to image_host, all on `stream`; returns after the image is in
- * host memory (the call synchronises the stream).  Staging buffers are
- * allocated on first use for max_pulses chirps (counted in the HBM budget).
+ * image back to image_host; returns after the image is in host memory (the
+ * call synchronises `stream`).  The uploads run on a copy stream of the plan
+ * in two chunks of chirps, ordered after the work already queued on
+ * `stream`; the kernels run on `stream`, the first chunk's while the second
+ * chunk is still being copied.  Staging buffers are allocated on first use
+ * for max_pulses chirps (counted in the HBM budget).  Calls on one plan must
+ * not overlap.
  *  beat_host  complex64 [M][R][N];  w_az_host float [M] or NULL;
  *  q_tx_host  double [M][2];  q_rx_host double [M][R][2];
  *  image_host complex64 [n_pixels].
@@ -344,15 +354,29 @@ int sar_form_image_host(sar_plan *plan, const void *beat_host, int32_t M,
 
 /*
  * Autotuner of the backprojection launch shape (no counterpart in the paper):
- * times sar_backproject on these inputs for each candidate pair (CTAs per SM
- * the registers are sized for: 2 or 3; chirps per pipeline block: the
- * largest that fits that many CTAs' shared memory, 2/3 and 1/2 of it) and
- * keeps the fastest in the plan (see sar_plan_get_info).  image_dev is
- * overwritten.  Blocks until the timing runs on `stream` finish.  Results of
- * later calls do not depend on the choice beyond FP32 summation order.
+ * times sar_backproject on these inputs for each candidate shape (Rx group:
+ * the plan's default and the next smaller divisor of n_rx; CTAs per SM the
+ * registers are sized for: 2 or 3; chirps per pipeline block: the largest
+ * that fits that many CTAs' shared memory, 2/3 and 1/2 of it) and keeps the
+ * fastest in the plan (see sar_plan_get_info).  image_dev is overwritten.
+ * Blocks until the timing runs on `stream` finish.  Results of later calls do
+ * not depend on the choice beyond FP32 summation order.
  */
 int sar_plan_autotune(sar_plan *plan, const void *prof_dev, int32_t M, const double *q_tx_dev,
                       const double *q_rx_dev, void *image_dev, void *stream);
+
+/*
+ * Set the backprojection launch shape explicitly, e.g. one saved from
+ * sar_plan_get_info after sar_plan_autotune:
+ *  rx_group          Rx channels per inner-loop group: 1..4, dividing n_rx
+ *  regs_ctas_per_sm  2 or 3 (register budget of the kernel variant)
+ *  pulses_per_block  chirps staged per pipeline step, 1..32
+ * SAR_EINVAL if the shape is out of range or its shared memory does not
+ * allow one CTA per SM; the plan keeps its previous shape then.  Results do
+ * not depend on the shape beyond FP32 summation order.  Not thread-safe
+ * against calls that use the plan.
+ */
+int sar_plan_set_launch(sar_plan *plan, int32_t rx_group, int32_t regs_ctas_per_sm, int32_t pulses_per_block);
 
 /*
  * Waits for the plan's device work and reports (then clears) kernel-side

@@ -29,7 +29,7 @@ EXPORTS = (
     "sar_batch_create", "sar_batch_destroy", "sar_batch_clear", "sar_batch_add",
     "sar_batch_commit", "sar_batch_launch", "sar_batch_get_info",
     "sar_server_create", "sar_server_destroy", "sar_submit", "sar_poll", "sar_wait",
-    "sar_release", "sar_server_get_stats", "sar_plan_autotune",
+    "sar_release", "sar_server_get_stats", "sar_plan_autotune", "sar_plan_set_launch",
 )
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 
@@ -67,6 +67,7 @@ class PlanInfo(ctypes.Structure):
         ("window_bins", ctypes.c_int32), ("pulses_per_block", ctypes.c_int32),
         ("bp_ctas", ctypes.c_int32), ("bins_per_metre", ctypes.c_double),
         ("cycles_per_bin", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+        ("rx_group", ctypes.c_int32), ("regs_ctas_per_sm", ctypes.c_int32),
     ]
 
 
@@ -301,10 +302,22 @@ class Plan:
         """Pick the fastest backprojection launch shape on these inputs."""
         _check(self._lib.sar_plan_autotune(self._plan, _ptr(prof), M, _ptr(q_tx), _ptr(q_rx),
                                            _ptr(image), _stream(stream)), "sar_plan_autotune")
+        return self.launch_shape()
+
+    def launch_shape(self) -> dict:
+        """The backprojection launch shape the plan uses now."""
         _check(self._lib.sar_plan_get_info(self._plan, ctypes.byref(self.info)),
                "sar_plan_get_info")
-        return {"pulses_per_block": int(self.info.pulses_per_block),
+        return {"rx_group": int(self.info.rx_group),
+                "regs_ctas_per_sm": int(self.info.regs_ctas_per_sm),
+                "pulses_per_block": int(self.info.pulses_per_block),
                 "bp_ctas": int(self.info.bp_ctas)}
+
+    def set_launch(self, rx_group: int, regs_ctas_per_sm: int, pulses_per_block: int) -> dict:
+        """Install an explicit launch shape (e.g. one saved after autotune)."""
+        _check(self._lib.sar_plan_set_launch(self._plan, rx_group, regs_ctas_per_sm,
+                                             pulses_per_block), "sar_plan_set_launch")
+        return self.launch_shape()
 
     def check_errors(self) -> int:
         return self._lib.sar_plan_check_errors(self._plan)

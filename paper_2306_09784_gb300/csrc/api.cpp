@@ -49,6 +49,9 @@ struct sar_plan {
     float *s_waz = nullptr;
     double *s_qtx = nullptr, *s_qrx = nullptr;
     void *s_prof = nullptr, *s_img = nullptr;
+    // its copy stream and events (created on first use)
+    cudaStream_t s_copy = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_chunk[2] = {nullptr, nullptr};
     size_t budget = 0, used = 0;
     std::vector<void *> allocs;
 };
@@ -121,7 +124,42 @@ void free_plan(sar_plan *pl) {
     DeviceGuard g(pl->device);
     cudaDeviceSynchronize();
     for (void *p : pl->allocs) cudaFree(p);
+    if (pl->s_copy) cudaStreamDestroy(pl->s_copy);
+    for (cudaEvent_t e : {pl->ev_start, pl->ev_chunk[0], pl->ev_chunk[1]})
+        if (e) cudaEventDestroy(e);
     delete pl;
+}
+
+// Largest of 4, 3, 2, 1 that divides the Rx count.
+int default_rx_group(int R) { return (R % 4 == 0) ? 4 : (R % 3 == 0) ? 3 : (R % 2 == 0) ? 2 : 1; }
+
+// Validate and install a backprojection launch shape; the plan is unchanged
+// on failure.
+int apply_launch(sar_plan *pl, int rg, int minb, int Mb) {
+    if (rg < 1 || rg > 4 || pl->p.n_rx % rg != 0 || minb < 2 || minb > 3 || Mb < 1 || Mb > kMaxPulsesPerBlock)
+        return SAR_EINVAL;
+    const size_t smem = bp_smem_bytes(Mb, pl->p.n_rx, pl->L, pl->fp16);
+    if (smem > kBpSmemMax) return SAR_EINVAL;
+    if (bp_prepare(pl->fp16, rg, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return SAR_EINVAL;
+    }
+    int occ = 0;
+    if (bp_occupancy(pl->fp16, rg, smem, minb, &occ) != 0 || occ < 1) {
+        cudaGetLastError();
+        return SAR_EINVAL;
+    }
+    occ = std::min(occ, minb);
+    const int G = pl->num_sms * occ;
+    // split-tile slots of the worst case (one pulse block per tile)
+    if ((size_t)G * (size_t)(pl->n_tiles / G + 2) > pl->partial_slots) return SAR_EINVAL;
+    pl->rg = rg;
+    pl->minb = minb;
+    pl->Mb = Mb;
+    pl->bp_smem = smem;
+    pl->ctas_per_sm = occ;
+    pl->G = G;
+    return SAR_OK;
 }
 
 // Modified Bessel I0 from its power series.
@@ -347,6 +385,10 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
         return SAR_EINVAL;
     }
     pl->beta = p.f0 / (p.c * pl->a1);
+    if (!(pl->beta >= 1e-9 && pl->beta <= 1e9)) {  // the kernels scale by 2 pi beta and its inverse
+        delete pl;
+        return SAR_EINVAL;
+    }
     pl->fd_max = (float)p.max_doppler_bins;
 
     HostTiles ht;
@@ -362,7 +404,7 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
     int L = (int)std::ceil(span) + 2 * kGuardBins + 4;
     L = (L + 3) & ~3;
     pl->L = L;
-    pl->rg = (p.n_rx % 4 == 0) ? 4 : (p.n_rx % 3 == 0) ? 3 : (p.n_rx % 2 == 0) ? 2 : 1;
+    pl->rg = default_rx_group(p.n_rx);
     const size_t per_pulse = bp_smem_bytes(1, p.n_rx, L, pl->fp16);
     int Mb = (int)std::min<size_t>(kMaxPulsesPerBlock, std::max<size_t>(1, kBpSmemTarget / per_pulse));
     while (Mb > 1 && bp_smem_bytes(Mb, p.n_rx, L, pl->fp16) > kBpSmemTarget) --Mb;
@@ -443,7 +485,11 @@ size_t profile_bytes(const sar_plan *pl, int M) {
 
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-int rc_launch(sar_plan *pl, const void *beat, int M, const float *w_az, void *out, int mode, cudaStream_t s) {
+
+// Range compression of pulses [m0, m0 + M) of a profile buffer laid out for
+// M_tot pulses; `beat` and `w_az` point at pulse m0.
+int rc_launch_part(sar_plan *pl, const void *beat, int m0, int M, int M_tot, const float *w_az, void *out,
+                   int mode, cudaStream_t s) {
     RcArgs a{};
     a.beat = (const float2 *)beat;
     a.w_r = pl->d_wr;
@@ -457,34 +503,47 @@ int rc_launch(sar_plan *pl, const void *beat, int M, const float *w_az, void *ou
     a.log2n = pl->log2n;
     a.crop_lo = pl->crop_lo;
     a.n_bins = pl->n_bins;
+    const size_t r0 = (size_t)m0 * pl->p.n_rx;
     if (mode == kRcProfileF16) {
-        const size_t rows = (size_t)M * pl->p.n_rx;
-        a.scales = (float *)out;
-        a.out = (unsigned char *)out + ((rows * 4 + 255) & ~size_t(255));
+        const size_t rows = (size_t)M_tot * pl->p.n_rx;
+        a.scales = (float *)out + r0;
+        a.out = (unsigned char *)out + ((rows * 4 + 255) & ~size_t(255)) + r0 * pl->n_bins * 4;
+    } else if (mode == kRcProfileF32) {
+        a.out = (float2 *)out + r0 * pl->n_bins;
     } else {
-        a.out = out;
+        a.out = (float2 *)out + r0 * pl->n_fft;
     }
     DeviceGuard dg(pl->device);
     if (!dg.ok) return SAR_ECUDA;
     return launch_range_compress(a, pl->sign, mode, s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
 }
 
-int bp_launch(sar_plan *pl, const void *prof, int M, const double *q_tx, const double *q_rx, const float *fd,
-              void *image, int accumulate, cudaStream_t s) {
+int rc_launch(sar_plan *pl, const void *beat, int M, const float *w_az, void *out, int mode, cudaStream_t s) {
+    return rc_launch_part(pl, beat, 0, M, M, w_az, out, mode, s);
+}
+
+// Kernel arguments common to every backprojection launch of a plan: the
+// profile layout, geometry tables and phase constants.  The launch fields
+// (G, seg_max, partial) are left for the caller.
+// With M_tot > 0, the call covers pulses [m0, m0 + M) of a profile buffer
+// laid out for M_tot pulses, and q_tx, q_rx point at pulse m0.
+BpArgs common_bp_args(const sar_plan *pl, const void *prof, int M, const double *q_tx, const double *q_rx,
+                      const float *fd, void *image, int accumulate, int m0 = 0, int M_tot = 0) {
     BpArgs a{};
-    const size_t rows = (size_t)M * pl->p.n_rx;
+    if (M_tot <= 0) M_tot = M;
+    const size_t rows = (size_t)M_tot * pl->p.n_rx, r0 = (size_t)m0 * pl->p.n_rx;
     if (pl->fp16) {
-        a.prof_scale = (const float *)prof;
-        a.prof = (const unsigned char *)prof + ((rows * 4 + 255) & ~size_t(255));
+        a.prof_scale = (const float *)prof + r0;
+        a.prof = (const unsigned char *)prof + ((rows * 4 + 255) & ~size_t(255)) + r0 * pl->n_bins * 4;
     } else {
-        a.prof = prof;
+        a.prof = (const float2 *)prof + r0 * pl->n_bins;
         a.prof_scale = nullptr;
     }
     a.q_tx = q_tx;
     a.q_rx = q_rx;
     a.fdopp = fd;
     a.image = (float2 *)image;
-    a.partial = pl->d_partial;
+    a.partial = nullptr;
     a.err = pl->d_err;
     a.pix = pl->d_pix;
     a.out_idx = pl->d_out;
@@ -496,22 +555,47 @@ int bp_launch(sar_plan *pl, const void *prof, int M, const double *q_tx, const d
     a.L = pl->L;
     a.blocks_per_tile = (M + pl->Mb - 1) / pl->Mb;
     a.units = (long long)pl->n_tiles * a.blocks_per_tile;
-    a.G = (int)std::min<long long>(pl->G, a.units);
-    const long long per = (a.units + a.G - 1) / a.G;
-    a.seg_max = (int)((per - 1) / a.blocks_per_tile) + 2;
     a.n_bins = pl->n_bins;
     a.crop_lo = pl->crop_lo;
     a.crop_hi = pl->crop_hi;
     a.accumulate = accumulate ? 1 : 0;
     a.a1 = pl->a1;
     a.a1f = (float)pl->a1;
-    a.two_pi_beta = (float)(pl->sign * 2.0 * kPi * pl->beta);
+    // kappa = sign 2 pi beta rounded to 22 significant bits, so that
+    // kappa * 1.5 * 2^23 is exact in FP32 (the kernel's fractional-phase step
+    // relies on it); the relative change is below 2.4e-7.
+    int ex = 0;
+    const double mant = std::frexp(pl->sign * 2.0 * kPi * pl->beta, &ex);
+    const float kap = (float)std::ldexp(std::nearbyint(std::ldexp(mant, 22)), ex - 22);
+    a.kappa = kap;
+    a.kappa_magic = (float)((double)kap * 12582912.0);
     a.beta = (float)pl->beta;
     a.sign = (float)pl->sign;
     const double cb = -pl->sign * 2.0 * kPi * (pl->beta - std::floor(pl->beta));
-    a.cb = make_float2((float)std::cos(cb), (float)std::sin(cb));
+    a.cb_k = make_float2((float)(std::cos(cb) / kap), (float)(std::sin(cb) / kap));
+    a.inv_kappa = (float)(1.0 / kap);
     a.fd_max = pl->fd_max;
-    if ((size_t)a.G * a.seg_max > pl->partial_slots) return SAR_EINVAL;  // cannot happen
+    a.div_nq = ((1ull << 32) + (unsigned)(pl->L / 4) - 1) / (unsigned)(pl->L / 4);
+    a.div_r = ((1ull << 32) + (unsigned)pl->p.n_rx - 1) / (unsigned)pl->p.n_rx;
+    a.fp16 = pl->fp16 ? 1 : 0;
+    a.rg = pl->rg;
+    return a;
+}
+
+// Persistent grid and split-tile slots of one launch over `slots` partial
+// sums.  Returns false when the decomposition needs more slots.
+bool set_launch(const sar_plan *pl, BpArgs &a, float2 *partial, size_t slots) {
+    a.G = (int)std::min<long long>(pl->G, a.units);
+    const long long per = (a.units + a.G - 1) / a.G;
+    a.seg_max = (int)((per - 1) / a.blocks_per_tile) + 2;
+    a.partial = partial;
+    return (size_t)a.G * (size_t)a.seg_max <= slots;
+}
+
+int bp_launch(sar_plan *pl, const void *prof, int M, const double *q_tx, const double *q_rx, const float *fd,
+              void *image, int accumulate, cudaStream_t s, int m0 = 0, int M_tot = 0) {
+    BpArgs a = common_bp_args(pl, prof, M, q_tx, q_rx, fd, image, accumulate, m0, M_tot);
+    if (!set_launch(pl, a, pl->d_partial, pl->partial_slots)) return SAR_EINVAL;  // cannot happen
     BpLaunch l{pl->rg, pl->fp16, pl->bp_smem, pl->minb};
     DeviceGuard dg(pl->device);
     if (!dg.ok) return SAR_ECUDA;
@@ -530,48 +614,7 @@ int fill_bp_args(const sar_plan *pl, const void *prof, int M, const double *q_tx
                  void *image, int accumulate, BpArgs *out, size_t *smem) {
     if (!pl || !prof || !q_tx || !q_rx || !image || M < 1 || M > pl->p.max_pulses) return SAR_EINVAL;
     if (!aligned(prof, 256) || !aligned(q_tx, 16) || !aligned(q_rx, 16) || !aligned(image, 8)) return SAR_EINVAL;
-    BpArgs a{};
-    const size_t rows = (size_t)M * pl->p.n_rx;
-    if (pl->fp16) {
-        a.prof_scale = (const float *)prof;
-        a.prof = (const unsigned char *)prof + ((rows * 4 + 255) & ~size_t(255));
-    } else {
-        a.prof = prof;
-        a.prof_scale = nullptr;
-    }
-    a.q_tx = q_tx;
-    a.q_rx = q_rx;
-    a.fdopp = nullptr;
-    a.image = (float2 *)image;
-    a.partial = nullptr;
-    a.err = pl->d_err;
-    a.pix = pl->d_pix;
-    a.out_idx = pl->d_out;
-    a.tiles = pl->d_tiles;
-    a.M = M;
-    a.R = pl->p.n_rx;
-    a.n_tiles = pl->n_tiles;
-    a.Mb = pl->Mb;
-    a.L = pl->L;
-    a.blocks_per_tile = (M + pl->Mb - 1) / pl->Mb;
-    a.units = (long long)pl->n_tiles * a.blocks_per_tile;
-    a.G = 0;
-    a.seg_max = 0;
-    a.n_bins = pl->n_bins;
-    a.crop_lo = pl->crop_lo;
-    a.crop_hi = pl->crop_hi;
-    a.accumulate = accumulate ? 1 : 0;
-    a.a1 = pl->a1;
-    a.a1f = (float)pl->a1;
-    a.two_pi_beta = (float)(pl->sign * 2.0 * kPi * pl->beta);
-    a.beta = (float)pl->beta;
-    a.sign = (float)pl->sign;
-    const double cb = -pl->sign * 2.0 * kPi * (pl->beta - std::floor(pl->beta));
-    a.cb = make_float2((float)std::cos(cb), (float)std::sin(cb));
-    a.fd_max = pl->fd_max;
-    a.fp16 = pl->fp16 ? 1 : 0;
-    a.rg = pl->rg;
-    *out = a;
+    *out = common_bp_args(pl, prof, M, q_tx, q_rx, nullptr, image, accumulate);
     *smem = pl->bp_smem;
     return SAR_OK;
 }
@@ -584,48 +627,8 @@ int backproject_with_scratch(sar_plan *pl, const void *prof, int M, const double
                              cudaStream_t s) {
     if (!pl || M < 1 || M > pl->p.max_pulses) return SAR_EINVAL;
     if (fd && !(pl->fd_max > 0)) return SAR_EINVAL;
-    BpArgs a{};
-    const size_t rows = (size_t)M * pl->p.n_rx;
-    if (pl->fp16) {
-        a.prof_scale = (const float *)prof;
-        a.prof = (const unsigned char *)prof + ((rows * 4 + 255) & ~size_t(255));
-    } else {
-        a.prof = prof;
-        a.prof_scale = nullptr;
-    }
-    a.q_tx = q_tx;
-    a.q_rx = q_rx;
-    a.fdopp = fd;
-    a.image = (float2 *)image;
-    a.partial = scratch;
-    a.err = pl->d_err;
-    a.pix = pl->d_pix;
-    a.out_idx = pl->d_out;
-    a.tiles = pl->d_tiles;
-    a.M = M;
-    a.R = pl->p.n_rx;
-    a.n_tiles = pl->n_tiles;
-    a.Mb = pl->Mb;
-    a.L = pl->L;
-    a.blocks_per_tile = (M + pl->Mb - 1) / pl->Mb;
-    a.units = (long long)pl->n_tiles * a.blocks_per_tile;
-    a.G = (int)std::min<long long>(pl->G, a.units);
-    const long long per = (a.units + a.G - 1) / a.G;
-    a.seg_max = (int)((per - 1) / a.blocks_per_tile) + 2;
-    a.n_bins = pl->n_bins;
-    a.crop_lo = pl->crop_lo;
-    a.crop_hi = pl->crop_hi;
-    a.accumulate = accumulate ? 1 : 0;
-    a.a1 = pl->a1;
-    a.a1f = (float)pl->a1;
-    a.two_pi_beta = (float)(pl->sign * 2.0 * kPi * pl->beta);
-    a.beta = (float)pl->beta;
-    a.sign = (float)pl->sign;
-    const double cb = -pl->sign * 2.0 * kPi * (pl->beta - std::floor(pl->beta));
-    a.cb = make_float2((float)std::cos(cb), (float)std::sin(cb));
-    a.fd_max = pl->fd_max;
-    const size_t need = (size_t)a.G * (size_t)a.seg_max * kTilePx * sizeof(float2);
-    if (need > scratch_bytes) return SAR_ESCRATCH;
+    BpArgs a = common_bp_args(pl, prof, M, q_tx, q_rx, fd, image, accumulate);
+    if (!set_launch(pl, a, scratch, scratch_bytes / (kTilePx * sizeof(float2)))) return SAR_ESCRATCH;
     BpLaunch l{pl->rg, pl->fp16, pl->bp_smem, pl->minb};
     DeviceGuard dg(pl->device);
     if (!dg.ok) return SAR_ECUDA;
@@ -683,6 +686,8 @@ int sar_plan_get_info(const sar_plan *pl, sar_plan_info *info) {
     i.bins_per_metre = pl->a1;
     i.cycles_per_bin = pl->beta;
     i.device_bytes = pl->used;
+    i.rx_group = pl->rg;
+    i.regs_ctas_per_sm = pl->minb;
     *info = i;
     return SAR_OK;
 }
@@ -742,18 +747,50 @@ int sar_form_image_host(sar_plan *pl, const void *beat_host, int32_t M, const fl
             return rc;
         }
     }
+    if (!pl->s_copy) {
+        if (cudaStreamCreateWithFlags(&pl->s_copy, cudaStreamNonBlocking) != cudaSuccess) {
+            pl->s_copy = nullptr;
+            return SAR_ECUDA;
+        }
+        for (cudaEvent_t *e : {&pl->ev_start, &pl->ev_chunk[0], &pl->ev_chunk[1]})
+            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return SAR_ECUDA;
+    }
     cudaStream_t s = (cudaStream_t)stream;
-    bool ok = cudaMemcpyAsync(pl->s_beat, beat_host, (size_t)M * R * N * 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    // Two-chunk pipeline: the copy stream uploads the trajectory, w_sar and
+    // the first ~1/8 of the chirps (whole pulse blocks), then the rest; the
+    // caller's stream range-compresses and backprojects the first chunk while
+    // the rest is still in flight, then the rest (accumulating into the image).
+    int cut = (M / 8) / pl->Mb * pl->Mb;
+    if (cut < pl->Mb || cut >= M) cut = M;
+    const int bounds[3] = {0, cut, M};
+    const int n_chunks = cut < M ? 2 : 1;
+    const size_t row_bytes = (size_t)R * N * 8;
+    bool ok = cudaEventRecord(pl->ev_start, s) == cudaSuccess &&
+              cudaStreamWaitEvent(pl->s_copy, pl->ev_start, 0) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(pl->s_qtx, q_tx_host, (size_t)M * 16, cudaMemcpyHostToDevice, pl->s_copy) == cudaSuccess;
+    ok = ok &&
+         cudaMemcpyAsync(pl->s_qrx, q_rx_host, (size_t)M * R * 16, cudaMemcpyHostToDevice, pl->s_copy) == cudaSuccess;
     if (w_az_host)
-        ok = ok && cudaMemcpyAsync(pl->s_waz, w_az_host, (size_t)M * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
-    ok = ok && cudaMemcpyAsync(pl->s_qtx, q_tx_host, (size_t)M * 16, cudaMemcpyHostToDevice, s) == cudaSuccess;
-    ok = ok && cudaMemcpyAsync(pl->s_qrx, q_rx_host, (size_t)M * R * 16, cudaMemcpyHostToDevice, s) == cudaSuccess;
+        ok = ok &&
+             cudaMemcpyAsync(pl->s_waz, w_az_host, (size_t)M * 4, cudaMemcpyHostToDevice, pl->s_copy) == cudaSuccess;
+    for (int c = 0; c < n_chunks && ok; ++c) {
+        const size_t off = (size_t)bounds[c] * row_bytes, bytes = (size_t)(bounds[c + 1] - bounds[c]) * row_bytes;
+        ok = cudaMemcpyAsync((unsigned char *)pl->s_beat + off, (const unsigned char *)beat_host + off, bytes,
+                             cudaMemcpyHostToDevice, pl->s_copy) == cudaSuccess &&
+             cudaEventRecord(pl->ev_chunk[c], pl->s_copy) == cudaSuccess;
+    }
     if (!ok) return SAR_ECUDA;
-    rc = rc_launch(pl, pl->s_beat, M, w_az_host ? pl->s_waz : nullptr, pl->s_prof,
-                   pl->fp16 ? kRcProfileF16 : kRcProfileF32, s);
-    if (rc) return rc;
-    rc = bp_launch(pl, pl->s_prof, M, pl->s_qtx, pl->s_qrx, nullptr, pl->s_img, 0, s);
-    if (rc) return rc;
+    const int mode = pl->fp16 ? kRcProfileF16 : kRcProfileF32;
+    for (int c = 0; c < n_chunks; ++c) {
+        const int m0 = bounds[c], Mc = bounds[c + 1] - bounds[c];
+        if (cudaStreamWaitEvent(s, pl->ev_chunk[c], 0) != cudaSuccess) return SAR_ECUDA;
+        rc = rc_launch_part(pl, (const unsigned char *)pl->s_beat + (size_t)m0 * row_bytes, m0, Mc, M,
+                            w_az_host ? pl->s_waz + m0 : nullptr, pl->s_prof, mode, s);
+        if (rc) return rc;
+        rc = bp_launch(pl, pl->s_prof, Mc, pl->s_qtx + 2 * (size_t)m0, pl->s_qrx + 2 * (size_t)m0 * R, nullptr,
+                       pl->s_img, c > 0, s, m0, M);
+        if (rc) return rc;
+    }
     if (cudaMemcpyAsync(image_host, pl->s_img, (size_t)pl->n_pixels * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return SAR_ECUDA;
     return cudaStreamSynchronize(s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
@@ -957,46 +994,40 @@ int sar_plan_autotune(sar_plan *pl, const void *prof_dev, int32_t M, const doubl
     if (!dg.ok) return SAR_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
     struct Cfg {
-        int minb, Mb, G;
-        size_t smem;
+        int rg, minb, Mb;
     };
     std::vector<Cfg> cands;
+    const int R = pl->p.n_rx;
+    const int rg0 = default_rx_group(R);
+    int rg1 = 0;
+    for (int g = rg0 - 1; g >= 1 && !rg1; --g)
+        if (R % g == 0) rg1 = g;
     const size_t budgets[2] = {kBpSmemTarget, 73 * 1024};
-    for (int minb = 2; minb <= 3; ++minb) {
-        int mb_max = 0;
-        for (int mb = kMaxPulsesPerBlock; mb >= 1; --mb)
-            if (bp_smem_bytes(mb, pl->p.n_rx, pl->L, pl->fp16) <= budgets[minb - 2]) {
-                mb_max = mb;
-                break;
+    for (int rg : {rg0, rg1}) {
+        if (rg < 1) continue;
+        for (int minb = 2; minb <= 3; ++minb) {
+            int mb_max = 0;
+            for (int mb = kMaxPulsesPerBlock; mb >= 1; --mb)
+                if (bp_smem_bytes(mb, R, pl->L, pl->fp16) <= budgets[minb - 2]) {
+                    mb_max = mb;
+                    break;
+                }
+            if (mb_max == 0) continue;
+            for (int mb : {mb_max, std::max(1, (mb_max * 2) / 3), std::max(1, mb_max / 2)}) {
+                bool dup = false;
+                for (const Cfg &d : cands) dup |= (d.rg == rg && d.minb == minb && d.Mb == mb);
+                if (!dup) cands.push_back(Cfg{rg, minb, mb});
             }
-        if (mb_max == 0) continue;
-        for (int mb : {mb_max, std::max(1, (mb_max * 2) / 3), std::max(1, mb_max / 2)}) {
-            const size_t smem = bp_smem_bytes(mb, pl->p.n_rx, pl->L, pl->fp16);
-            int occ = 0;
-            if (bp_occupancy(pl->fp16, pl->rg, smem, minb, &occ) != 0 || occ < 1) {
-                cudaGetLastError();
-                continue;
-            }
-            occ = std::min(occ, minb);
-            const Cfg c{minb, mb, pl->num_sms * occ, smem};
-            bool dup = false;
-            for (const Cfg &d : cands) dup |= (d.minb == c.minb && d.Mb == c.Mb);
-            if (!dup) cands.push_back(c);
         }
     }
-    if (cands.empty()) return SAR_EINVAL;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SAR_ECUDA;
-    const int save_minb = pl->minb, save_mb = pl->Mb, save_g = pl->G;
-    const size_t save_smem = pl->bp_smem;
+    const Cfg saved{pl->rg, pl->minb, pl->Mb};
     float best = 1e30f;
-    Cfg best_c{save_minb, save_mb, save_g, save_smem};
+    Cfg best_c = saved;
     int rc = SAR_OK;
     for (const Cfg &c : cands) {
-        pl->minb = c.minb;
-        pl->Mb = c.Mb;
-        pl->G = c.G;
-        pl->bp_smem = c.smem;
+        if (apply_launch(pl, c.rg, c.minb, c.Mb) != SAR_OK) continue;  // does not fit: skip
         float times[3];
         for (int rep = -1; rep < 3 && rc == SAR_OK; ++rep) {
             if (rep >= 0 && cudaEventRecord(e0, s) != cudaSuccess) rc = SAR_ECUDA;
@@ -1016,12 +1047,16 @@ int sar_plan_autotune(sar_plan *pl, const void *prof_dev, int32_t M, const doubl
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    pl->minb = rc ? save_minb : best_c.minb;
-    pl->Mb = rc ? save_mb : best_c.Mb;
-    pl->G = rc ? save_g : best_c.G;
-    pl->bp_smem = rc ? save_smem : best_c.smem;
-    pl->ctas_per_sm = pl->G / pl->num_sms;
+    const Cfg fin = rc ? saved : best_c;
+    if (apply_launch(pl, fin.rg, fin.minb, fin.Mb) != SAR_OK && !rc) rc = SAR_ECUDA;
     return rc;
+}
+
+int sar_plan_set_launch(sar_plan *pl, int32_t rx_group, int32_t regs_ctas_per_sm, int32_t pulses_per_block) {
+    if (!pl) return SAR_EINVAL;
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return SAR_ECUDA;
+    return apply_launch(pl, rx_group, regs_ctas_per_sm, pulses_per_block);
 }
 
 int sar_plan_check_errors(sar_plan *pl) {

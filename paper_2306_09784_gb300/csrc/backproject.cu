@@ -21,8 +21,11 @@
 //    compression) and exp(sign j 2 pi beta f) of the fractional index f.
 //  * The bins a tile can touch for one (pulse, Rx) form a short window
 //    (a few tens of bins).  Windows of a block of pulses are staged in shared
-//    memory as (A_k, D_k) = rot_k (S_k, S_{k+1} - S_k) pairs, so one 16-byte
-//    shared load feeds an update: v = A + f D.
+//    memory as (A_k, D_k) = rot_k (S_k, (S_{k+1} - S_k) / kappa) pairs,
+//    kappa = sign 2 pi beta, so one 16-byte shared load feeds an update:
+//    with g = kappa f the phase, v = A + g D.  g comes from the index in two
+//    FMAs (kappa has 22 significant bits, so kappa floor(idx) is formed
+//    exactly from the magic-number floor).
 //  * Two inner loops, chosen per (tile, pulse block) by the FP64 stage:
 //    - expansion loop (the common case): Rx antennas lie millimetres from the
 //      Tx antenna, so with o = q_rx - q_tx and a = |o|^2 / 2 - (p - q_tx).o,
@@ -81,10 +84,6 @@ __host__ __device__ inline Layout bp_layout(int Mb, int R, int L, bool fp16) {
     off += 16u;
     s.total = off;
     return s;
-}
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
 template <int BYTES>
@@ -224,20 +223,21 @@ __device__ __forceinline__ int prep_block(const BpArgs &a, const Smem &sm, const
             const int m = m0 + p;
             const double2 qt = reinterpret_cast<const double2 *>(a.q_tx)[m];
             const double2 qr = reinterpret_cast<const double2 *>(a.q_rx)[(long long)m * R + r];
-            const double wx = ti.x - qt.x, wy = ti.y - qt.y;
-            const double ox = qr.x - qt.x, oy = qr.y - qt.y;
-            const double o2 = ox * ox + oy * oy;
-            const double cexp = 0.5 * o2 - (wx * ox + wy * oy);
+            // differences in FP64, the rest in FP32: the a / d term carries a
+            // relative error of a few 1e-7, i.e. ~1e-7 bins
+            const float wx = (float)(ti.x - qt.x), wy = (float)(ti.y - qt.y);
+            const float ox = (float)(qr.x - qt.x), oy = (float)(qr.y - qt.y);
+            const float o2 = fmaf(ox, ox, oy * oy);
+            const float cexp = fmaf(0.5f, o2, -fmaf(wx, ox, wy * oy));
             const uint32_t addr_c = table_addr + (uint32_t)(task * a.L) * 16u - kMagicBits * 16u;
             // halved so that the pixel loop gets a / 2 directly
-            rxt[task] = make_float4((float)(-0.5 * ox), (float)(-0.5 * oy), (float)(0.5 * cexp),
-                                    __uint_as_float(addr_c));
-            if (!(fabs(oy) <= 1e-9)) exact |= kFlagOffAxis;
+            rxt[task] = make_float4(-0.5f * ox, -0.5f * oy, 0.5f * cexp, __uint_as_float(addr_c));
+            if (!(fabsf(oy) <= 1e-9f)) exact |= kFlagOffAxis;
             const float scale = a.prof_scale ? __ldg(a.prof_scale + (long long)m * R + r) : 1.0f;
             pr[task].w = __float_as_int(scale);
             // path criteria (FP32 is plenty; non-finite input fails them)
-            const float rt = hypotf((float)wx, (float)wy);
-            const float oa = sqrtf((float)o2);
+            const float rt = hypotf(wx, wy);
+            const float oa = sqrtf(o2);
             const float dmin = rt - rho;
             const bool expand = rt > 2.0f * rho + oa + 1e-3f && rt < (float)kMaxRange &&
                                 oa <= (float)o_allow && (float)o2 * oa <= tol2 * dmin * dmin;
@@ -297,6 +297,11 @@ __device__ __forceinline__ int window_start(const Smem &sm, int cslot, int Mb, i
     return exact ? sm.pair(cslot, MbR)[w].z : sm.txc(cslot, Mb)[p].y;
 }
 
+// floor(n / d) for 0 <= n, n d < 2^32, from mul = ceil(2^32 / d).
+__device__ __forceinline__ int fast_div(int n, unsigned long long mul) {
+    return (int)(((unsigned long long)(unsigned)n * mul) >> 32);
+}
+
 // Issue cp.async copies of the raw profile samples of one pulse block.  Item
 // = (window w, group q of 4 entries) = samples k_lo + 4q .. k_lo + 4q + 4.
 // Samples outside [crop_lo, crop_hi] are zero-filled.
@@ -309,26 +314,35 @@ __device__ __forceinline__ void stage_block(const BpArgs &a, const Smem &sm, int
     const unsigned char *prof = reinterpret_cast<const unsigned char *>(a.prof);
     const uint32_t raw = sm.base_addr + sm.lay.raw;
     const int n_items = np * R * nq;
+    const long long row0 = (long long)b * MbR;  // window w reads profile row row0 + w
     for (int it = threadIdx.x; it < n_items; it += blockDim.x) {
-        const int w = it / nq;
+        const int w = fast_div(it, a.div_nq);
         const int q = it - w * nq;
-        const int p = w / R;
-        const int r = w - p * R;
-        const long long row = (long long)(b * Mb + p) * R + r;
-        const unsigned char *rowp = prof + row * a.n_bins * SB;
+        const int p = exact ? 0 : fast_div(w, a.div_r);
         const int k0 = window_start(sm, cslot, Mb, MbR, w, p, exact) + 4 * q;
+        // sample k of this row sits at prof + (base + k) * SB
+        const long long base = (row0 + w) * a.n_bins - a.crop_lo;
         const uint32_t dst = raw + (uint32_t)it * 5u * SB;
+        if (k0 >= a.crop_lo && k0 + 4 <= a.crop_hi) {
+            const unsigned char *src = prof + (base + k0) * SB;
 #pragma unroll
-        for (int e = 0; e < 5; ++e) {
-            const int k = k0 + e;
-            const bool ok = (k >= a.crop_lo) && (k <= a.crop_hi);
-            const void *src = ok ? (const void *)(rowp + (long long)(k - a.crop_lo) * SB) : a.prof;
-            cp_async<SB>(dst + e * SB, src, ok ? SB : 0);
+            for (int e = 0; e < 5; ++e) cp_async<SB>(dst + e * SB, src + e * SB, SB);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 5; ++e) {
+                const int k = k0 + e;
+                const bool ok = (k >= a.crop_lo) && (k <= a.crop_hi);
+                const void *src = ok ? (const void *)(prof + (base + k) * SB) : a.prof;
+                cp_async<SB>(dst + e * SB, src, ok ? SB : 0);
+            }
         }
     }
 }
 
-// Convert this thread's staged raw samples into (A, D) table entries.
+// Convert this thread's staged raw samples into (A, D) table entries:
+// A = S_k, D = (S_{k+1} exp(-sign j 2 pi beta) - S_k) / kappa (the stored
+// samples carry the per-bin rotation already).  Entries whose base bin lies
+// outside [crop_lo, crop_hi) are zero.
 template <bool FP16>
 __device__ __forceinline__ void convert_block(const BpArgs &a, const Smem &sm, int b, int cslot, int tslot,
                                               bool exact) {
@@ -341,9 +355,9 @@ __device__ __forceinline__ void convert_block(const BpArgs &a, const Smem &sm, i
     const unsigned char *raw = sm.base + sm.lay.raw;
     const int n_items = np * R * nq;
     for (int it = threadIdx.x; it < n_items; it += blockDim.x) {
-        const int w = it / nq;
+        const int w = fast_div(it, a.div_nq);
         const int q = it - w * nq;
-        const int p = w / R;
+        const int p = exact ? 0 : fast_div(w, a.div_r);
         const int k0 = window_start(sm, cslot, Mb, MbR, w, p, exact) + 4 * q;
         float2 s[5];
         if (FP16) {
@@ -360,27 +374,35 @@ __device__ __forceinline__ void convert_block(const BpArgs &a, const Smem &sm, i
             for (int e = 0; e < 5; ++e) s[e] = f[e];
         }
         float4 *dst = table + w * a.L + 4 * q;
+        const float2 cbk = a.cb_k;
+        const float ik = a.inv_kappa;
+        const bool inside = k0 >= a.crop_lo && k0 + 3 < a.crop_hi;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int k = k0 + e;
-            const bool valid = (k >= a.crop_lo) && (k < a.crop_hi);
-            const float2 nb = cmul(s[e + 1], a.cb);
-            const float4 ent = make_float4(s[e].x, s[e].y, nb.x - s[e].x, nb.y - s[e].y);
+            const bool valid = inside || ((k >= a.crop_lo) && (k < a.crop_hi));
+            const float dre = fmaf(s[e + 1].x, cbk.x, fmaf(-s[e + 1].y, cbk.y, -s[e].x * ik));
+            const float dim = fmaf(s[e + 1].x, cbk.y, fmaf(s[e + 1].y, cbk.x, -s[e].y * ik));
+            const float4 ent = make_float4(s[e].x, s[e].y, dre, dim);
             dst[e] = valid ? ent : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
 }
 
-// One update: interpolate entry (A, D) at fractional index f and accumulate
-// (A + f D) exp(sign j 2 pi beta f).
-__device__ __forceinline__ void accumulate(float idx, uint32_t ac, float k2pb, float &acc_re, float &acc_im) {
+// One update: with f the fractional part of idx and g = kappa f, interpolate
+// entry (A, D) as A + g D and accumulate it times exp(j g).  tm = 1.5 2^23 +
+// floor(idx) exactly; kapm = kappa 1.5 2^23 is exact, so fma(-kappa, tm, kapm)
+// = -kappa floor(idx) with one rounding, and g = fma(idx, kappa, that) with
+// one more (absolute error ~ ulp(kappa L), a few 1e-4 rad at most).
+__device__ __forceinline__ void accumulate(float idx, uint32_t ac, float kap, float kapm, float &acc_re,
+                                           float &acc_im) {
     const float tm = __fadd_rd(idx, kMagic);
-    const float f = idx - (tm - kMagic);
+    const float g = fmaf(idx, kap, fmaf(-kap, tm, kapm));
     const float4 e = lds128((__float_as_uint(tm) << 4) + ac);
-    const float vre = fmaf(f, e.z, e.x);
-    const float vim = fmaf(f, e.w, e.y);
+    const float vre = fmaf(g, e.z, e.x);
+    const float vim = fmaf(g, e.w, e.y);
     float sn, cs;
-    sincos_approx(f * k2pb, sn, cs);
+    sincos_approx(g, sn, cs);
     acc_re = fmaf(vre, cs, acc_re);
     acc_im = fmaf(vre, sn, acc_im);
     acc_re = fmaf(-vim, sn, acc_re);
@@ -401,7 +423,7 @@ __device__ __forceinline__ void expand_pulses(const BpArgs &a, const float4 *txr
                                               float (&acc_im)[kPxPerThread]) {
     const int R = a.R;
     const float two_a1 = 2.0f * a.a1f;
-    const float k2pb = a.two_pi_beta;
+    const float kap = a.kappa, kapm = a.kappa_magic;
     float u[PU][kPxPerThread], ay[PU][kPxPerThread], kk[PU][kPxPerThread];
 #pragma unroll
     for (int q = 0; q < PU; ++q) {
@@ -431,7 +453,7 @@ __device__ __forceinline__ void expand_pulses(const BpArgs &a, const float4 *txr
                     const float w = AXIS ? fmaf(o4.x, dx[j], o4.z) : fmaf(o4.x, dx[j], fmaf(o4.y, dy[j], o4.z));
                     const float m1 = fmaf(-w, kk[q][j], ay[q][j]);
                     const float idx = fmaf(w, m1, u[q][j]);
-                    accumulate(idx, ac, k2pb, acc_re[j], acc_im[j]);
+                    accumulate(idx, ac, kap, kapm, acc_re[j], acc_im[j]);
                 }
             }
         }
@@ -480,7 +502,7 @@ __device__ __forceinline__ void compute_block_exact(const BpArgs &a, const Smem 
     const float4 *rxr = sm.rxr(cslot, MbR);
     const int4 *pr = sm.pair(cslot, MbR);
     const float a1 = a.a1f;
-    const float k2pb = a.two_pi_beta;
+    const float kap = a.kappa, kapm = a.kappa_magic;
     const float lmax = (float)(a.L - 2);
     for (int p = 0; p < np; ++p) {
         const float4 t4 = txr[p];
@@ -505,7 +527,7 @@ __device__ __forceinline__ void compute_block_exact(const BpArgs &a, const Smem 
                     float idx = fmaf(a1, dt[j] + drx, idx0);
                     if (FD) idx += fdi[j];
                     idx = fminf(fmaxf(idx, 0.0f), lmax);
-                    accumulate(idx, ac, k2pb, acc_re[j], acc_im[j]);
+                    accumulate(idx, ac, kap, kapm, acc_re[j], acc_im[j]);
                 }
             }
         }

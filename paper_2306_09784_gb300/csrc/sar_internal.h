@@ -70,11 +70,15 @@ struct BpArgs {
     int accumulate;
     double a1;                 // bins per metre
     float a1f;
-    float two_pi_beta;         // sign * 2 pi beta (radians per bin)
+    float kappa;               // sign * 2 pi beta (radians per bin), 22 significant bits
+    float kappa_magic;         // kappa * 1.5 * 2^23 (exact)
+    float inv_kappa;           // 1 / kappa
     float beta;                // cycles per bin
     float sign;
-    float2 cb;                 // exp(-sign j 2 pi beta)
+    float2 cb_k;               // exp(-sign j 2 pi beta) / kappa
     float fd_max;              // bound on |f_doppler|
+    unsigned long long div_nq; // ceil(2^32 / (L / 4)): division by the groups per window
+    unsigned long long div_r;  // ceil(2^32 / R)
     int fp16;                  // profile storage (batched form)
     int rg;                    // Rx group of the inner loop (batched form)
 };

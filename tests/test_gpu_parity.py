@@ -445,6 +445,43 @@ def test_autotune_keeps_results(torch, small):
     assert rel_l2(after, oracle_image(wl, beat, w_az)) <= TOL_FP16
 
 
+def test_set_launch_shapes(torch):
+    """Every valid launch shape gives the same image within FP32 summation
+    order; shapes out of range are rejected and leave the plan unchanged."""
+    import paper_2306_09784_gb300 as sar
+    radar = synth.Radar(n_samples=128, n_rx=4, os=4)
+    M = 40
+    rng = np.random.Generator(np.random.PCG64(77))
+    q_tx, q_rx = synth.trajectory(radar, M, jitter=0.01, rng=rng)
+    grid = synth.Grid(-1.0, 2.0, 0.04, 0.04, 50, 41)
+    tg = np.stack([rng.uniform(-0.9, 0.9, 5), rng.uniform(2.1, 3.5, 5)], 1)
+    am = rng.standard_normal(5) + 1j * rng.standard_normal(5)
+    wl = synth.Workload("shapes", radar, M, grid, q_tx, q_rx, tg, am, 20.0, 3,
+                        synth.crop_for(radar, grid, q_tx, q_rx))
+    beat = synth.workload_beat(wl)
+    w_az = np.hanning(M)
+    plan = make_plan(wl, precision=0)
+    ref = gpu_image(plan, wl, beat, w_az)
+    assert rel_l2(ref, oracle_image(wl, beat, w_az)) <= TOL_FP32
+    default = plan.launch_shape()
+    assert default["rx_group"] == 4
+    for rg in (1, 2, 4):
+        for minb in (2, 3):
+            for mb in (1, 7, 16):
+                shape = plan.set_launch(rg, minb, mb)
+                assert (shape["rx_group"], shape["regs_ctas_per_sm"], shape["pulses_per_block"]) == \
+                    (rg, minb, mb)
+                img = gpu_image(plan, wl, beat, w_az)
+                assert rel_l2(img, ref) < 1e-5, shape
+    before = plan.launch_shape()
+    for bad in ((3, 2, 8), (0, 2, 8), (5, 2, 8), (4, 1, 8), (4, 4, 8), (4, 2, 0), (4, 2, 33)):
+        with pytest.raises(sar.SarError) as e:
+            plan.set_launch(*bad)
+        assert e.value.status == sar.SAR_EINVAL
+        assert plan.launch_shape() == before
+    assert plan.check_errors() == sar.SAR_OK
+
+
 def test_off_axis_rx_array(torch):
     """Rx array tilted 30 degrees off the driving direction: the expansion
     loop takes its general (x and y offset) form."""
