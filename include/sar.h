@@ -358,9 +358,13 @@ int sar_form_image_host(sar_plan *plan, const void *beat_host, int32_t M,
  * the plan's default and the next smaller divisor of n_rx; CTAs per SM the
  * registers are sized for: 2 or 3; chirps per pipeline block: the largest
  * that fits that many CTAs' shared memory, 2/3 and 1/2 of it) and keeps the
- * fastest in the plan (see sar_plan_get_info).  image_dev is overwritten.
- * Blocks until the timing runs on `stream` finish.  Results of later calls do
- * not depend on the choice beyond FP32 summation order.
+ * fastest in the plan (see sar_plan_get_info).  The choice is also
+ * remembered for the process, keyed by device, Rx count, staged window
+ * length, profile storage, and max_pulses and tile count rounded up to
+ * powers of two: plans created later with the same key start from it.
+ * image_dev is overwritten.  Blocks until the timing runs on `stream`
+ * finish.  Results of later calls do not depend on the choice beyond FP32
+ * summation order.
  */
 int sar_plan_autotune(sar_plan *plan, const void *prof_dev, int32_t M, const double *q_tx_dev,
                       const double *q_rx_dev, void *image_dev, void *stream);

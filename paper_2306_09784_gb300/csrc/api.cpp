@@ -4,7 +4,10 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <numeric>
 #include <vector>
 
@@ -160,6 +163,44 @@ int apply_launch(sar_plan *pl, int rg, int minb, int Mb) {
     pl->ctas_per_sm = occ;
     pl->G = G;
     return SAR_OK;
+}
+
+// Launch shapes chosen by sar_plan_autotune, remembered for the process and
+// keyed by what the shape depends on: device, Rx count, window length,
+// storage, and max_pulses and tile count rounded up to powers of two.
+using ShapeKey = std::tuple<int, int, int, int, int, int>;
+struct Shape {
+    int rg, minb, Mb;
+};
+std::mutex g_shape_mu;
+std::map<ShapeKey, Shape> g_shapes;
+
+int pow2_ceil(long long v) {
+    int e = 0;
+    while ((1ll << e) < v && e < 62) ++e;
+    return e;
+}
+
+ShapeKey shape_key(const sar_plan *pl) {
+    return ShapeKey{pl->device, pl->p.n_rx, pl->L, pl->fp16 ? 1 : 0, pow2_ceil(pl->p.max_pulses),
+                    pow2_ceil(pl->n_tiles)};
+}
+
+void remember_shape(const sar_plan *pl) {
+    std::lock_guard<std::mutex> g(g_shape_mu);
+    g_shapes[shape_key(pl)] = Shape{pl->rg, pl->minb, pl->Mb};
+}
+
+// Start a new plan from a remembered shape, if there is one that fits.
+void recall_shape(sar_plan *pl) {
+    Shape sh{};
+    {
+        std::lock_guard<std::mutex> g(g_shape_mu);
+        auto it = g_shapes.find(shape_key(pl));
+        if (it == g_shapes.end()) return;
+        sh = it->second;
+    }
+    apply_launch(pl, sh.rg, sh.minb, sh.Mb);  // the plan keeps its default shape if this fails
 }
 
 // Modified Bessel I0 from its power series.
@@ -404,6 +445,12 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
     int L = (int)std::ceil(span) + 2 * kGuardBins + 4;
     L = (L + 3) & ~3;
     pl->L = L;
+    for (TileInfo &ti : ht.tiles) {
+        const double o_allow = ((double)(L - 3 - 2 * kGuardBins) - 2.0 * pl->fd_max - 4.0 * ti.rho * pl->a1) /
+                               (2.0 * pl->a1);
+        ti.o_allow = (float)o_allow;
+        ti.klo_off = (float)(pl->a1 * (2.0 * ti.rho + o_allow) + pl->fd_max);
+    }
     pl->rg = default_rx_group(p.n_rx);
     const size_t per_pulse = bp_smem_bytes(1, p.n_rx, L, pl->fp16);
     int Mb = (int)std::min<size_t>(kMaxPulsesPerBlock, std::max<size_t>(1, kBpSmemTarget / per_pulse));
@@ -435,6 +482,7 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
         pl->seg_cap = pl->n_tiles / g_min + 2;
         pl->partial_slots = (size_t)g_max * pl->seg_cap;
     }
+    recall_shape(pl);
 
     // FP64 tables
     std::vector<float> wr = range_window(p.range_window, p.n_samples, p.kaiser_beta);
@@ -1049,6 +1097,7 @@ int sar_plan_autotune(sar_plan *pl, const void *prof_dev, int32_t M, const doubl
     cudaEventDestroy(e1);
     const Cfg fin = rc ? saved : best_c;
     if (apply_launch(pl, fin.rg, fin.minb, fin.Mb) != SAR_OK && !rc) rc = SAR_ECUDA;
+    if (!rc) remember_shape(pl);
     return rc;
 }
 

@@ -121,9 +121,10 @@ __device__ __forceinline__ void sincos_approx(float x, float &s, float &c) {
 __device__ __forceinline__ double sqrt_fp64(double x) {
     // outside the seed's range: tiny -> 0, huge stays huge (rejected later as
     // beyond the maximum range), negative or NaN -> NaN
-    if (!(x >= 1e-30 && x <= 1e30))
+    const float xf = (float)x;
+    if (!(xf >= 1e-30f && xf <= 1e30f))
         return x >= 0.0 ? (x < 1e-30 ? 0.0 : x) : __longlong_as_double(0x7ff8000000000000ll);
-    const double y = (double)rsqrt_approx((float)x);
+    const double y = (double)rsqrt_approx(xf);
     const double r = x * y;
     return fma(0.5 * y, fma(-r, r, x), r);
 }
@@ -185,25 +186,25 @@ __device__ __forceinline__ int prep_block(const BpArgs &a, const Smem &sm, const
     const int m0 = b * Mb;
     const int np = min(Mb, a.M - m0);
     const int rx_base = ((Mb + 31) >> 5) << 5;
-    // largest Rx offset the common window of the expansion loop absorbs
-    const double o_allow = ((double)(a.L - 3 - 2 * kGuardBins) - 2.0 * a.fd_max - 4.0 * ti.rho * a.a1) /
-                           (2.0 * a.a1);
     const int t = threadIdx.x;
     if (t < rx_base) {
         float4 *txr = sm.txr(cslot, Mb);
         int4 *txc = sm.txc(cslot, Mb);
         for (int p = t; p < np; p += rx_base) {
+            // FP64 where FP32 would lose the index: the differences, the
+            // range, the window start and 2 a1 R_tx - k_lo
             const double2 qt = reinterpret_cast<const double2 *>(a.q_tx)[m0 + p];
             const double wx = ti.x - qt.x, wy = ti.y - qt.y;
-            const double r_tx = sqrt_fp64(wx * wx + wy * wy);
-            const bool ok = isfinite(r_tx) && r_tx < kMaxRange;
+            const double r2 = fma(wx, wx, wy * wy);
+            const double r_tx = sqrt_fp64(r2);
+            const float r_f = (float)r_tx;
+            const bool ok = r_f < (float)kMaxRange;  // false for NaN and inf
             float4 t4 = make_float4(0.f, 0.f, 1.f, 1.f);
             int4 c = make_int4(0, -(1 << 30), 0, 0);
             if (ok) {
-                t4 = make_float4((float)wx, (float)wy, (float)r_tx, (float)(r_tx * r_tx));
-                const int k_lo =
-                    (int)floor(a.a1 * (2.0 * r_tx - 2.0 * ti.rho - o_allow) - (double)a.fd_max) - kGuardBins;
-                c = make_int4(__float_as_int((float)(2.0 * a.a1 * r_tx - (double)k_lo)), k_lo, 0, 0);
+                t4 = make_float4((float)wx, (float)wy, r_f, (float)r2);
+                const int k_lo = __double2int_rd(fma(2.0 * a.a1, r_tx, -(double)ti.klo_off)) - kGuardBins;
+                c = make_int4(__float_as_int((float)fma(2.0 * a.a1, r_tx, -(double)k_lo)), k_lo, 0, 0);
             } else {
                 exact = kFlagExact;
             }
@@ -240,7 +241,7 @@ __device__ __forceinline__ int prep_block(const BpArgs &a, const Smem &sm, const
             const float oa = sqrtf(o2);
             const float dmin = rt - rho;
             const bool expand = rt > 2.0f * rho + oa + 1e-3f && rt < (float)kMaxRange &&
-                                oa <= (float)o_allow && (float)o2 * oa <= tol2 * dmin * dmin;
+                                oa <= ti.o_allow && (float)o2 * oa <= tol2 * dmin * dmin;
             exact |= expand ? 0 : kFlagExact;
         }
     }
@@ -461,8 +462,9 @@ __device__ __forceinline__ void expand_pulses(const BpArgs &a, const float4 *txr
 }
 
 // Expansion loop over one pulse block (far field, small Rx offsets).  When
-// all Rx channels of a pulse fit one group (R == RG < 3), 4 / RG pulses are
-// processed together; the per-pixel summation order stays pulse by pulse.
+// all Rx channels of a pulse fit one group (R == RG), 4 / RG pulses (2 for
+// RG >= 3) are processed together; the per-pixel summation order stays pulse
+// by pulse.
 template <int RG, bool FD, bool AXIS>
 __device__ __forceinline__ void compute_block_expand(const BpArgs &a, const Smem &sm, int b, int cslot,
                                                      const float (&dx)[kPxPerThread],
@@ -471,7 +473,7 @@ __device__ __forceinline__ void compute_block_expand(const BpArgs &a, const Smem
                                                      const float (&fdi)[kPxPerThread],
                                                      float (&acc_re)[kPxPerThread],
                                                      float (&acc_im)[kPxPerThread]) {
-    constexpr int PU = RG >= 3 ? 1 : 4 / RG;
+    constexpr int PU = RG >= 3 ? 2 : 4 / RG;
     const int R = a.R, Mb = a.Mb, MbR = Mb * R;
     const int np = min(Mb, a.M - b * Mb);
     const float4 *txr = sm.txr(cslot, Mb);

@@ -42,9 +42,13 @@ struct RcArgs {
 cudaError_t launch_range_compress(const RcArgs &a, int sign, int mode, cudaStream_t s);
 
 // Per-tile data: reference point (x, y), radius rho (max distance of the
-// tile's points from the reference), number of valid points.
+// tile's points from the reference), number of valid points, and two
+// plan-dependent constants of the expansion loop: o_allow, the largest Rx
+// offset (m) the common window absorbs, and klo_off = a1 (2 rho + o_allow) +
+// fd_max, so that a pulse's window starts at floor(2 a1 R_tx - klo_off) - G.
 struct TileInfo {
     double x, y, rho;
+    float o_allow, klo_off;
     int32_t n_valid;
     int32_t pad;
 };

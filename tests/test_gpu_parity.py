@@ -445,6 +445,21 @@ def test_autotune_keeps_results(torch, small):
     assert rel_l2(after, oracle_image(wl, beat, w_az)) <= TOL_FP16
 
 
+def test_autotuned_shape_is_remembered(torch, small):
+    """A plan created after sar_plan_autotune with the same key (device, Rx
+    count, window, storage, size buckets) starts from the tuned shape."""
+    wl, beat, w_az = small
+    plan = make_plan(wl, precision=1)
+    b, w, qt, qr = to_dev(wl, beat, w_az)
+    prof = plan.range_compress(b, w)
+    scratch = torch.zeros(plan.n_pixels, dtype=torch.complex64, device="cuda")
+    tuned = plan.autotune(prof, wl.n_pulses, qt, qr, scratch)
+    again = make_plan(wl, precision=1)
+    assert again.launch_shape() == tuned
+    img = gpu_image(again, wl, beat, w_az)
+    assert rel_l2(img, gpu_image(plan, wl, beat, w_az)) < 1e-6
+
+
 def test_set_launch_shapes(torch):
     """Every valid launch shape gives the same image within FP32 summation
     order; shapes out of range are rejected and leave the plan unchanged."""
