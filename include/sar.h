@@ -230,18 +230,21 @@ int sar_backproject_noalloc(sar_plan *plan, const void *prof_dev, int32_t M,
                             int32_t accumulate, void *stream);
 
 /*
- * Batched backprojection (Alg. 2 for several requests in one launch).
+ * Batched backprojection (Alg. 2 for several requests in few launches).
  * Requests of uneven sizes -- each with its own plan (radar parameters,
  * reconstruction points, FP32 or FP16 profiles), profiles, trajectory and
  * image -- are packed as (request, pixel tile, pulse block) work units and
- * split evenly over one persistent grid; tiles shared by two CTAs are summed
- * by a fix-up kernel.  Each request's image equals sar_backproject's up to
- * FP32 summation order.
+ * split evenly over one persistent grid per class of requests that share an
+ * Rx group and a profile storage (at most 8 classes; the pixel loop is
+ * specialised per class); tiles shared by two CTAs are summed by a fix-up
+ * kernel.  Each request's image equals sar_backproject's up to FP32
+ * summation order.
  *
- * Use: sar_batch_clear, sar_batch_add per request, sar_batch_commit (uploads
- * the request table on `stream`), then sar_batch_launch (two kernels on
- * `stream`, reading only device memory: it can be captured in a CUDA graph
- * and replayed while the table and the request buffers stay unchanged).
+ * Use: sar_batch_clear, sar_batch_add per request, sar_batch_commit (groups
+ * the requests by class and uploads the request table on `stream`), then
+ * sar_batch_launch (two kernels per class on `stream`, reading only device
+ * memory: it can be captured in a CUDA graph and replayed while the table
+ * and the request buffers stay unchanged).
  * All plans of a batch must be on the batch's device; the batch owns its
  * request table (pinned host + device) and 16 KB of scratch per CTA.
  * Requests of one batch must not write the same image.
@@ -259,9 +262,10 @@ int sar_batch_add(sar_batch *batch, sar_plan *plan, const void *prof_dev, int32_
                   int32_t accumulate);
 /* Upload the request table asynchronously on `stream`. */
 int sar_batch_commit(sar_batch *batch, void *stream);
-/* Launch the persistent backprojection and its fix-up over all requests. */
+/* Launch the persistent backprojection and its fix-up for each class of requests. */
 int sar_batch_launch(sar_batch *batch, void *stream);
-/* Requests, work units and CTAs of the committed batch (any pointer may be NULL). */
+/* Requests, work units and the largest class grid (CTAs) of the committed
+ * batch (any pointer may be NULL). */
 int sar_batch_get_info(const sar_batch *batch, int32_t *n_jobs, int64_t *units, int32_t *ctas);
 
 /*

@@ -59,22 +59,38 @@ struct sar_plan {
     std::vector<void *> allocs;
 };
 
+// One persistent launch per class of requests with the same Rx group and
+// profile storage (the kernel is specialised on both).
+struct BatchClass {
+    int rg = 0;
+    bool fp16 = false;
+    int j0 = 0, n = 0;       // jobs [j0, j0 + n) of the sorted table
+    int off = 0;             // first entry of its prefix sums (j0 + class index)
+    long long units = 0;
+    int tiles = 0, G = 0;
+    size_t smem = 0;
+};
+
+constexpr int kBatchClasses = 8;  // Rx group 1..4 x storage
+
 struct sar_batch {
     int device = 0;
     int max_jobs = 0, n_jobs = 0;
     int num_sms = 0, g_cap = 0, G = 0;
     long long units = 0;
     int tiles = 0;
-    size_t smem = 0;
     bool committed = false, upload_pending = false;
-    BpArgs *h_jobs = nullptr;
-    long long *h_ub = nullptr;
-    int *h_tb = nullptr;
+    BpArgs *h_jobs = nullptr;    // in the order added
+    BpArgs *h_sorted = nullptr;  // grouped by class (upload source)
+    long long *h_ub = nullptr;   // per-class prefix sums of units
+    int *h_tb = nullptr;         // per-class prefix sums of tiles
     BpArgs *d_jobs = nullptr;
     long long *d_ub = nullptr;
     int *d_tb = nullptr;
     float2 *d_scratch = nullptr;
     cudaEvent_t uploaded = nullptr;
+    int n_classes = 0;
+    BatchClass cls[kBatchClasses];
 };
 
 namespace {
@@ -861,12 +877,14 @@ int sar_batch_create(int32_t max_jobs, sar_batch **out) {
     }
     b->num_sms = prop.multiProcessorCount;
     b->g_cap = b->num_sms * 2;  // the batch kernel runs at most two CTAs per SM
+    const size_t n_pref = (size_t)max_jobs + kBatchClasses;
     bool ok = cudaMallocHost((void **)&b->h_jobs, sizeof(BpArgs) * max_jobs) == cudaSuccess &&
-              cudaMallocHost((void **)&b->h_ub, sizeof(long long) * (max_jobs + 1)) == cudaSuccess &&
-              cudaMallocHost((void **)&b->h_tb, sizeof(int) * (max_jobs + 1)) == cudaSuccess &&
+              cudaMallocHost((void **)&b->h_sorted, sizeof(BpArgs) * max_jobs) == cudaSuccess &&
+              cudaMallocHost((void **)&b->h_ub, sizeof(long long) * n_pref) == cudaSuccess &&
+              cudaMallocHost((void **)&b->h_tb, sizeof(int) * n_pref) == cudaSuccess &&
               cudaMalloc((void **)&b->d_jobs, sizeof(BpArgs) * max_jobs) == cudaSuccess &&
-              cudaMalloc((void **)&b->d_ub, sizeof(long long) * (max_jobs + 1)) == cudaSuccess &&
-              cudaMalloc((void **)&b->d_tb, sizeof(int) * (max_jobs + 1)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_ub, sizeof(long long) * n_pref) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_tb, sizeof(int) * n_pref) == cudaSuccess &&
               cudaMalloc((void **)&b->d_scratch, sizeof(float2) * kTilePx * 2 * (size_t)b->g_cap) == cudaSuccess &&
               cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
@@ -882,6 +900,7 @@ void sar_batch_destroy(sar_batch *b) {
     if (!b) return;
     cudaDeviceSynchronize();
     if (b->h_jobs) cudaFreeHost(b->h_jobs);
+    if (b->h_sorted) cudaFreeHost(b->h_sorted);
     if (b->h_ub) cudaFreeHost(b->h_ub);
     if (b->h_tb) cudaFreeHost(b->h_tb);
     if (b->d_jobs) cudaFree(b->d_jobs);
@@ -900,7 +919,7 @@ int sar_batch_clear(sar_batch *b) {
     b->n_jobs = 0;
     b->units = 0;
     b->tiles = 0;
-    b->smem = 0;
+    b->n_classes = 0;
     b->committed = false;
     return SAR_OK;
 }
@@ -917,12 +936,10 @@ int sar_batch_add(sar_batch *b, sar_plan *plan, const void *prof_dev, int32_t M,
     size_t smem = 0;
     const int rc = fill_bp_args(plan, prof_dev, M, q_tx_dev, q_rx_dev, image_dev, accumulate, &a, &smem);
     if (rc) return rc;
+    (void)smem;
     b->h_jobs[b->n_jobs] = a;
-    b->h_ub[b->n_jobs] = b->units;
-    b->h_tb[b->n_jobs] = b->tiles;
     b->units += a.units;
     b->tiles += a.n_tiles;
-    b->smem = std::max(b->smem, smem);
     b->n_jobs += 1;
     b->committed = false;
     return SAR_OK;
@@ -936,21 +953,55 @@ int sar_batch_commit(sar_batch *b, void *stream) {
     }
     DeviceGuard dg(b->device);
     if (!dg.ok) return SAR_ECUDA;
-    b->h_ub[b->n_jobs] = b->units;
-    b->h_tb[b->n_jobs] = b->tiles;
-    int occ = 0;
-    if (bp_batch_prepare(b->smem, &occ) != cudaSuccess || occ < 1) {
-        cudaGetLastError();
-        return SAR_ECUDA;
+    // group the jobs by class, keeping their order within a class
+    int count[kBatchClasses] = {0};
+    auto key = [](const BpArgs &a) { return (a.fp16 ? 4 : 0) + a.rg - 1; };
+    for (int j = 0; j < b->n_jobs; ++j) ++count[key(b->h_jobs[j])];
+    int fill[kBatchClasses];
+    b->n_classes = 0;
+    for (int k = 0, j0 = 0; k < kBatchClasses; ++k) {
+        fill[k] = j0;
+        if (count[k]) {
+            BatchClass &c = b->cls[b->n_classes];
+            c = BatchClass{};
+            c.rg = k % 4 + 1;
+            c.fp16 = k >= 4;
+            c.j0 = j0;
+            c.n = count[k];
+            c.off = j0 + b->n_classes;
+            ++b->n_classes;
+        }
+        j0 += count[k];
     }
-    b->G = (int)std::min<long long>(std::min(b->g_cap, b->num_sms * occ), b->units);
+    for (int j = 0; j < b->n_jobs; ++j) b->h_sorted[fill[key(b->h_jobs[j])]++] = b->h_jobs[j];
+    b->G = 0;
+    for (int ci = 0; ci < b->n_classes; ++ci) {
+        BatchClass &c = b->cls[ci];
+        for (int i = 0; i < c.n; ++i) {
+            const BpArgs &a = b->h_sorted[c.j0 + i];
+            b->h_ub[c.off + i] = c.units;
+            b->h_tb[c.off + i] = c.tiles;
+            c.units += a.units;
+            c.tiles += a.n_tiles;
+            c.smem = std::max(c.smem, bp_smem_bytes(a.Mb, a.R, a.L, c.fp16));
+        }
+        b->h_ub[c.off + c.n] = c.units;
+        b->h_tb[c.off + c.n] = c.tiles;
+        int occ = 0;
+        if (bp_batch_prepare(c.rg, c.fp16, c.smem, &occ) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            return SAR_ECUDA;
+        }
+        c.G = (int)std::min<long long>(std::min(b->g_cap, b->num_sms * occ), c.units);
+        b->G = std::max(b->G, c.G);
+    }
+    const int n_pref = b->n_jobs + b->n_classes;
     cudaStream_t s = (cudaStream_t)stream;
-    bool ok = cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(BpArgs) * b->n_jobs, cudaMemcpyHostToDevice, s) ==
+    bool ok = cudaMemcpyAsync(b->d_jobs, b->h_sorted, sizeof(BpArgs) * b->n_jobs, cudaMemcpyHostToDevice, s) ==
                   cudaSuccess &&
-              cudaMemcpyAsync(b->d_ub, b->h_ub, sizeof(long long) * (b->n_jobs + 1), cudaMemcpyHostToDevice, s) ==
+              cudaMemcpyAsync(b->d_ub, b->h_ub, sizeof(long long) * n_pref, cudaMemcpyHostToDevice, s) ==
                   cudaSuccess &&
-              cudaMemcpyAsync(b->d_tb, b->h_tb, sizeof(int) * (b->n_jobs + 1), cudaMemcpyHostToDevice, s) ==
-                  cudaSuccess &&
+              cudaMemcpyAsync(b->d_tb, b->h_tb, sizeof(int) * n_pref, cudaMemcpyHostToDevice, s) == cudaSuccess &&
               cudaEventRecord(b->uploaded, s) == cudaSuccess;
     if (!ok) return SAR_ECUDA;
     b->upload_pending = true;
@@ -963,16 +1014,20 @@ int sar_batch_launch(sar_batch *b, void *stream) {
     if (b->n_jobs == 0) return SAR_OK;
     DeviceGuard dg(b->device);
     if (!dg.ok) return SAR_ECUDA;
-    BpBatchArgs a{};
-    a.jobs = b->d_jobs;
-    a.unit_begin = b->d_ub;
-    a.tile_begin = b->d_tb;
-    a.scratch = b->d_scratch;
-    a.units = b->units;
-    a.n_jobs = b->n_jobs;
-    a.G = b->G;
-    return launch_backproject_batch(a, b->tiles, b->smem, (cudaStream_t)stream) == cudaSuccess ? SAR_OK
-                                                                                                 : SAR_ECUDA;
+    for (int ci = 0; ci < b->n_classes; ++ci) {
+        const BatchClass &c = b->cls[ci];
+        BpBatchArgs a{};
+        a.jobs = b->d_jobs + c.j0;
+        a.unit_begin = b->d_ub + c.off;
+        a.tile_begin = b->d_tb + c.off;
+        a.scratch = b->d_scratch;  // launches on one stream: the slots are reused in turn
+        a.units = c.units;
+        a.n_jobs = c.n;
+        a.G = c.G;
+        if (launch_backproject_batch(a, c.rg, c.fp16, c.tiles, c.smem, (cudaStream_t)stream) != cudaSuccess)
+            return SAR_ECUDA;
+    }
+    return SAR_OK;
 }
 
 }  // extern "C"
@@ -999,12 +1054,10 @@ int batch_add_rows(sar_batch *b, sar_plan *plan, const void *samples, const floa
     if (rc) return rc;
     a.prof = samples;
     a.prof_scale = plan->fp16 ? scales : nullptr;
+    (void)smem;
     b->h_jobs[b->n_jobs] = a;
-    b->h_ub[b->n_jobs] = b->units;
-    b->h_tb[b->n_jobs] = b->tiles;
     b->units += a.units;
     b->tiles += a.n_tiles;
-    b->smem = std::max(b->smem, smem);
     b->n_jobs += 1;
     b->committed = false;
     return SAR_OK;

@@ -672,9 +672,12 @@ __global__ void __launch_bounds__(kBpThreads, MINB) backproject_kernel(BpArgs a)
 
 // Batched form: the (request, tile, pulse block) units of several requests,
 // each with its own plan, profiles, trajectory and image, concatenated and
-// split into equal contiguous ranges over one persistent grid.  Only the
-// first and the last segment of a CTA's range can cover part of a tile, so
-// each CTA owns two partial-sum slots (0: first segment, 1: last segment).
+// split into equal contiguous ranges over one persistent grid.  One launch
+// covers the requests of one (Rx group, storage) class, so the pixel loop is
+// specialised like the single-request kernel.  Only the first and the last
+// segment of a CTA's range can cover part of a tile, so each CTA owns two
+// partial-sum slots (0: first segment, 1: last segment).
+template <int RG, bool FP16>
 __global__ void __launch_bounds__(kBpThreads, 2) backproject_batch_kernel(BpBatchArgs B) {
     extern __shared__ __align__(16) unsigned char smem_bp[];
     Smem sm;
@@ -693,7 +696,7 @@ __global__ void __launch_bounds__(kBpThreads, 2) backproject_batch_kernel(BpBatc
     while (u < u1) {
         while (u >= B.unit_begin[j + 1]) ++j;
         const BpArgs a = B.jobs[j];
-        sm.lay = bp_layout(a.Mb, a.R, a.L, a.fp16 != 0);
+        sm.lay = bp_layout(a.Mb, a.R, a.L, FP16);
         const long long v = u - B.unit_begin[j];
         const int PB = a.blocks_per_tile;
         const int tile = (int)(v / PB);
@@ -701,17 +704,7 @@ __global__ void __launch_bounds__(kBpThreads, 2) backproject_batch_kernel(BpBatc
         const int b1 = (int)min((long long)PB, (long long)b0 + (u1 - u));
         float2 *dst = nullptr;
         if (!(b0 == 0 && b1 == PB)) dst = B.scratch + ((long long)blockIdx.x * 2 + (u == u0 ? 0 : 1)) * kTilePx;
-        if (a.fp16) {
-            if (a.rg == 4) process_segment<4, true, false>(a, sm, tile, b0, b1, dst);
-            else if (a.rg == 3) process_segment<3, true, false>(a, sm, tile, b0, b1, dst);
-            else if (a.rg == 2) process_segment<2, true, false>(a, sm, tile, b0, b1, dst);
-            else process_segment<1, true, false>(a, sm, tile, b0, b1, dst);
-        } else {
-            if (a.rg == 4) process_segment<4, false, false>(a, sm, tile, b0, b1, dst);
-            else if (a.rg == 3) process_segment<3, false, false>(a, sm, tile, b0, b1, dst);
-            else if (a.rg == 2) process_segment<2, false, false>(a, sm, tile, b0, b1, dst);
-            else process_segment<1, false, false>(a, sm, tile, b0, b1, dst);
-        }
+        process_segment<RG, FP16, false>(a, sm, tile, b0, b1, dst);
         u += b1 - b0;
     }
 }
@@ -830,18 +823,37 @@ int bp_occupancy(bool fp16, int rg, size_t smem, int minb, int *ctas_per_sm) {
     return 0;
 }
 
-cudaError_t bp_batch_prepare(size_t smem, int *ctas_per_sm) {
-    if (smem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(backproject_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemLimit);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, backproject_batch_kernel, kBpThreads, smem);
+namespace {
+
+void *select_batch_kernel(int rg, bool fp16) {
+#define SAR_SELB(RGV) \
+    if (rg == RGV) return fp16 ? (void *)backproject_batch_kernel<RGV, true> : (void *)backproject_batch_kernel<RGV, false>;
+    SAR_SELB(1)
+    SAR_SELB(2)
+    SAR_SELB(3)
+    SAR_SELB(4)
+#undef SAR_SELB
+    return nullptr;
 }
 
-cudaError_t launch_backproject_batch(const BpBatchArgs &b, int total_tiles, size_t smem, cudaStream_t s) {
+}  // namespace
+
+cudaError_t bp_batch_prepare(int rg, bool fp16, size_t smem, int *ctas_per_sm) {
+    void *k = select_batch_kernel(rg, fp16);
+    if (!k || smem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k, kBpThreads, smem);
+}
+
+cudaError_t launch_backproject_batch(const BpBatchArgs &b, int rg, bool fp16, int total_tiles, size_t smem,
+                                     cudaStream_t s) {
     if (b.units == 0 || b.n_jobs == 0) return cudaSuccess;
-    backproject_batch_kernel<<<b.G, kBpThreads, smem, s>>>(b);
-    cudaError_t e = cudaGetLastError();
+    void *k = select_batch_kernel(rg, fp16);
+    if (!k) return cudaErrorInvalidValue;
+    BpBatchArgs args = b;
+    void *params[] = {&args};
+    cudaError_t e = cudaLaunchKernel(k, dim3(b.G), dim3(kBpThreads), params, smem, s);
     if (e != cudaSuccess) return e;
     bp_batch_fixup_kernel<<<total_tiles, 256, 0, s>>>(b);
     return cudaGetLastError();

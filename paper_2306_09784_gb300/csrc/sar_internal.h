@@ -110,8 +110,9 @@ size_t bp_smem_bytes(int Mb, int R, int L, bool fp16);
 cudaError_t bp_prepare(bool fp16, int rg, size_t smem);  // sets function attributes
 int bp_occupancy(bool fp16, int rg, size_t smem, int minb, int *ctas_per_sm);
 cudaError_t launch_backproject(const BpArgs &a, const BpLaunch &l, cudaStream_t s);
-cudaError_t bp_batch_prepare(size_t smem, int *ctas_per_sm);
-cudaError_t launch_backproject_batch(const BpBatchArgs &b, int total_tiles, size_t smem, cudaStream_t s);
+cudaError_t bp_batch_prepare(int rg, bool fp16, size_t smem, int *ctas_per_sm);
+cudaError_t launch_backproject_batch(const BpBatchArgs &b, int rg, bool fp16, int total_tiles, size_t smem,
+                                     cudaStream_t s);
 
 // Used by the server (serve.cpp).
 int batch_add_rows(sar_batch *b, sar_plan *plan, const void *samples, const float *scales, int32_t M,
