@@ -413,6 +413,12 @@ int validate_params(const sar_radar_params *p) {
     }
     if (!(p->max_doppler_bins >= 0) || p->max_doppler_bins > 64) return SAR_EINVAL;
     if (p->range_window == SAR_WINDOW_KAISER && !(p->kaiser_beta >= 0 && p->kaiser_beta < 100)) return SAR_EINVAL;
+    // bins per metre a1 and phase cycles per bin beta (the kernels scale by
+    // 2 pi beta and by its inverse)
+    const double a1 = p->slope * (double)nfft / (p->c * p->fs);
+    if (!(a1 > 0)) return SAR_EINVAL;
+    const double beta = p->f0 / (p->c * a1);
+    if (!(beta >= 1e-9 && beta <= 1e9)) return SAR_EINVAL;
     return SAR_OK;
 }
 
@@ -436,16 +442,8 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
     pl->n_bins = pl->crop_hi - pl->crop_lo + 1;
     pl->sign = p.phase_sign;
     pl->fp16 = p.precision == SAR_PREC_FP16;
-    pl->a1 = p.slope * pl->n_fft / (p.c * p.fs);
-    if (!(pl->a1 > 0)) {
-        delete pl;
-        return SAR_EINVAL;
-    }
-    pl->beta = p.f0 / (p.c * pl->a1);
-    if (!(pl->beta >= 1e-9 && pl->beta <= 1e9)) {  // the kernels scale by 2 pi beta and its inverse
-        delete pl;
-        return SAR_EINVAL;
-    }
+    pl->a1 = p.slope * pl->n_fft / (p.c * p.fs);  // validated positive
+    pl->beta = p.f0 / (p.c * pl->a1);              // validated in [1e-9, 1e9]
     pl->fd_max = (float)p.max_doppler_bins;
 
     HostTiles ht;

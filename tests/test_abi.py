@@ -67,6 +67,36 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.sar_plan_check_errors(None) == 1
 
 
+def test_plan_parameters_rejected_without_gpu(lib):
+    """Radar parameters are validated on the host before any CUDA call:
+    each bad value below gives SAR_EINVAL (1)."""
+    import paper_2306_09784_gb300 as sar
+    lib.sar_plan_create.restype = ctypes.c_int
+
+    def params(**kw):
+        p = dict(f0=77e9, slope=1e9 / 102.4e-6, fs=128 / 102.4e-6, c=299792458.0, n_samples=128,
+                 os=4, n_rx=4, max_pulses=64, range_window=1, precision=0, kaiser_beta=0.0,
+                 phase_sign=1, crop_lo=0, crop_hi=0, reserved=0, max_doppler_bins=0.0)
+        p.update(kw)
+        return sar.RadarParams(**p)
+
+    grid = sar.Grid(x0=-1.0, y0=2.0, dx=0.05, dy=0.05, nx=8, ny=8, pixels_xy=None, n_pixels=0)
+    bad = [dict(f0=0.0), dict(f0=float("nan")), dict(slope=0.0), dict(fs=-1.0), dict(c=0.0),
+           dict(n_samples=0), dict(os=3), dict(n_rx=0), dict(n_rx=65), dict(max_pulses=0),
+           dict(n_samples=8, os=4), dict(n_samples=8192, os=4), dict(range_window=3),
+           dict(precision=2), dict(phase_sign=0), dict(crop_lo=10, crop_hi=5),
+           dict(crop_lo=0, crop_hi=512), dict(max_doppler_bins=-1.0), dict(max_doppler_bins=100.0),
+           dict(range_window=2, kaiser_beta=-1.0),
+           dict(f0=1e-6),      # beta = f0 / (c a1) ~ 2.5e-15 cycles per bin
+           dict(f0=1e19),      # beta ~ 2.5e9
+           dict(slope=-1e9 / 102.4e-6)]  # a1 < 0
+    for kw in bad:
+        out = ctypes.c_void_p()
+        p = params(**kw)
+        assert lib.sar_plan_create(ctypes.byref(p), ctypes.byref(grid), 0, ctypes.byref(out)) == 1, kw
+        assert out.value is None
+
+
 def test_struct_layouts_match_header():
     import paper_2306_09784_gb300 as sar
     gcc = shutil.which("gcc")
