@@ -189,9 +189,10 @@ def test_translation_invariance(torch):
     assert rel_l2(img, ref) <= TOL_FP32
 
 
-@pytest.mark.parametrize("n_rx", [1, 2, 3, 4, 8])
+@pytest.mark.parametrize("n_rx", [1, 2, 3, 4, 8, 64])
 def test_rx_counts(torch, n_rx):
-    """Inner-loop Rx grouping (1, 2, 4) and ragged pulse blocks (M = 45)."""
+    """Inner-loop Rx grouping (1, 2, 3, 4), ragged pulse blocks (M = 45) and
+    the largest Rx count a plan accepts (64: one chirp per pipeline block)."""
     radar = synth.Radar(n_samples=128, n_rx=n_rx, os=4)
     M = 45
     rng = np.random.Generator(np.random.PCG64(n_rx))
@@ -315,6 +316,19 @@ def test_doppler_offsets(torch, small):
     plan = make_plan(wl, max_doppler_bins=2.0)
     img = gpu_image(plan, wl, beat, w_az, fdopp=fd)
     ref = oracle_image(wl, beat, w_az, fd_idx=fd.astype(np.float32).astype(np.float64))
+    assert rel_l2(img, ref) <= TOL_FP32
+
+
+def test_doppler_offsets_at_the_largest_bound(torch, small):
+    """max_doppler_bins at its limit (64 bins): the staged windows widen by
+    128 bins; offsets up to +-60 bins and beyond the bound (clamped)."""
+    wl, beat, w_az = small
+    rng = np.random.Generator(np.random.PCG64(6))
+    fd = rng.uniform(-70.0, 70.0, wl.grid.nx * wl.grid.ny)
+    plan = make_plan(wl, max_doppler_bins=64.0)
+    img = gpu_image(plan, wl, beat, w_az, fdopp=fd)
+    clamped = np.clip(fd.astype(np.float32), -64.0, 64.0).astype(np.float64)
+    ref = oracle_image(wl, beat, w_az, fd_idx=clamped)
     assert rel_l2(img, ref) <= TOL_FP32
 
 
