@@ -245,6 +245,10 @@ __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src, uint32_
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes)
                  : "memory");
 }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
 
 // Output stage shared by both kernels: spectrum, FP32 profile or FP16
 // profile (scale = row max / 2^14) of the row held in X.
@@ -292,14 +296,17 @@ __device__ __forceinline__ void store_row(const RcArgs &a, const float2 *X, long
 // Persistent form for N_fft <= 4096 (256 threads, 4096 / N_fft rows per
 // group).  Twiddles and window sit in shared memory for the CTA's lifetime;
 // the beat samples of the next row group are copied in with cp.async while
-// the current group is transformed.
-template <int SGN, int MODE>
+// the current group is transformed.  LOGN > 0: N_fft = 2^LOGN fixed at
+// compile time (index and twiddle arithmetic folds into constants); 0: any
+// size.
+template <int SGN, int MODE, int LOGN>
 __global__ void __launch_bounds__(256, 2) range_compress_persistent(RcArgs a, long long n_groups) {
     extern __shared__ float2 smem_rcp[];
     __shared__ int row_max[64];
-    const int n = a.n_fft, N = a.N;
+    const int n = LOGN ? (1 << LOGN) : a.n_fft, N = a.N;
+    const int log2n = LOGN ? LOGN : a.log2n;
     const int T = n >> 4;
-    const int rows_per = blockDim.x / T;
+    const int rows_per = 256 / T;  // launched with 256 threads
     const int lrow = threadIdx.x / T;
     const int tid = threadIdx.x - lrow * T;
     float2 *X = smem_rcp + (size_t)lrow * (n + n / 16);
@@ -311,14 +318,29 @@ __global__ void __launch_bounds__(256, 2) range_compress_persistent(RcArgs a, lo
     const uint32_t stage_addr = (uint32_t)__cvta_generic_to_shared(stage);
     const int per_group = rows_per * N;
 
+    // 16-byte copies of two samples when the beat cube is 16-byte aligned (N
+    // is a power of two >= 4, so every row and the staging buffer are too);
+    // 8-byte copies otherwise
+    const bool a16 = (reinterpret_cast<uintptr_t>(a.beat) & 15u) == 0;
     auto issue = [&](long long g, int buf) {
-        for (int i = threadIdx.x; i < per_group; i += blockDim.x) {
-            const int lr = i / N;
-            const int k = i - lr * N;
-            const long long row = g * rows_per + lr;
-            const bool ok = row < a.rows;
-            const void *src = ok ? (const void *)(a.beat + row * (long long)N + k) : (const void *)a.beat;
-            cp_async8(stage_addr + (uint32_t)(buf * per_group + i) * 8u, src, ok ? 8u : 0u);
+        if (a16) {
+            for (int e = 2 * threadIdx.x; e < per_group; e += 2 * blockDim.x) {
+                const int lr = rows_per == 1 ? 0 : e / N;
+                const int k = e - lr * N;
+                const long long row = g * rows_per + lr;
+                const bool ok = row < a.rows;
+                const void *src = ok ? (const void *)(a.beat + row * (long long)N + k) : (const void *)a.beat;
+                cp_async16(stage_addr + (uint32_t)(buf * per_group + e) * 8u, src, ok ? 16u : 0u);
+            }
+        } else {
+            for (int i = threadIdx.x; i < per_group; i += blockDim.x) {
+                const int lr = rows_per == 1 ? 0 : i / N;
+                const int k = i - lr * N;
+                const long long row = g * rows_per + lr;
+                const bool ok = row < a.rows;
+                const void *src = ok ? (const void *)(a.beat + row * (long long)N + k) : (const void *)a.beat;
+                cp_async8(stage_addr + (uint32_t)(buf * per_group + i) * 8u, src, ok ? 8u : 0u);
+            }
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
@@ -338,19 +360,25 @@ __global__ void __launch_bounds__(256, 2) range_compress_persistent(RcArgs a, lo
         const long long row = g * rows_per + lrow;
         const bool active = row < a.rows;
         const float2 *src = stage + (size_t)((it & 1) * rows_per + lrow) * N;
-        const int n16 = a.log2n >> 2;
-        const int rem = a.log2n & 3;
-        int Ns = 1;
-        for (int p = 0; p < n16; ++p) {
-            if (p == 0)
-                stockham_pass<16, SGN, true, true>(X, n, a.log2n, Ns, tid, T, active, tw, src, wr, N);
-            else
-                stockham_pass<16, SGN, false, true>(X, n, a.log2n, Ns, tid, T, active, tw, src, wr, N);
-            Ns <<= 4;
+        const int n16 = log2n >> 2;
+        const int rem = log2n & 3;
+        stockham_pass<16, SGN, true, true>(X, n, log2n, 1, tid, T, active, tw, src, wr, N);
+        int Ns = 16;
+        if (LOGN) {
+#pragma unroll
+            for (int p = 1; p < (LOGN >> 2); ++p) {
+                stockham_pass<16, SGN, false, true>(X, n, log2n, 1 << (4 * p), tid, T, active, tw, src, wr, N);
+            }
+            Ns = 1 << (4 * (LOGN >> 2));
+        } else {
+            for (int p = 1; p < n16; ++p) {
+                stockham_pass<16, SGN, false, true>(X, n, log2n, Ns, tid, T, active, tw, src, wr, N);
+                Ns <<= 4;
+            }
         }
-        if (rem == 1) stockham_pass<2, SGN, false, true>(X, n, a.log2n, Ns, tid, T, active, tw, src, wr, N);
-        if (rem == 2) stockham_pass<4, SGN, false, true>(X, n, a.log2n, Ns, tid, T, active, tw, src, wr, N);
-        if (rem == 3) stockham_pass<8, SGN, false, true>(X, n, a.log2n, Ns, tid, T, active, tw, src, wr, N);
+        if (rem == 1) stockham_pass<2, SGN, false, true>(X, n, log2n, Ns, tid, T, active, tw, src, wr, N);
+        if (rem == 2) stockham_pass<4, SGN, false, true>(X, n, log2n, Ns, tid, T, active, tw, src, wr, N);
+        if (rem == 3) stockham_pass<8, SGN, false, true>(X, n, log2n, Ns, tid, T, active, tw, src, wr, N);
         store_row<MODE>(a, X, row, active, tid, T, lrow, row_max);
         __syncthreads();  // X and this group's stage buffer are reused next
     }
@@ -365,7 +393,9 @@ cudaError_t launch_rc(const RcArgs &a, cudaStream_t s) {
         if (n_groups == 0) return cudaSuccess;
         const size_t smem = ((size_t)rows_per * (n + n / 16) + n + 2 * (size_t)rows_per * a.N) * sizeof(float2) +
                             (size_t)a.N * sizeof(float);
-        auto kern = range_compress_persistent<SGN, MODE>;
+        auto kern = n == 4096   ? range_compress_persistent<SGN, MODE, 12>
+                    : n == 2048 ? range_compress_persistent<SGN, MODE, 11>
+                                : range_compress_persistent<SGN, MODE, 0>;
         int dev = 0, sms = 0, optin = 0, occ = 0;
         cudaFuncAttributes fa;
         if (cudaGetDevice(&dev) != cudaSuccess ||
