@@ -71,10 +71,15 @@ __host__ __device__ constexpr int ilog2(int) {
 }
 
 // In-register DFT of RAD points, v[k] <- sum_n v[n] exp(SGN j 2 pi n k / RAD),
-// natural order in and out (radix-2 decimation in time).
-template <int RAD, int SGN>
+// natural order in and out (radix-2 decimation in time).  ZR < RAD: only
+// v[0..ZR) may be nonzero.  After the bit reversal those sit at multiples of
+// RAD / ZR, and the first log2(RAD / ZR) butterfly stages pair each of them
+// with zeros only, which copies it across its block: those stages become
+// register copies.
+template <int RAD, int SGN, int ZR = RAD>
 __device__ __forceinline__ void dft_reg(float2 *v) {
     constexpr int bits = ilog2<RAD>(0);
+    constexpr int H0 = RAD / ZR;
 #pragma unroll
     for (int i = 0; i < RAD; ++i) {
         const int j = bitrev(i, bits);
@@ -84,8 +89,14 @@ __device__ __forceinline__ void dft_reg(float2 *v) {
             v[j] = t;
         }
     }
+    if (H0 > 1) {
 #pragma unroll
-    for (int h = 1; h < RAD; h <<= 1) {
+        for (int p = 0; p < RAD; p += H0)
+#pragma unroll
+            for (int i = 1; i < H0; ++i) v[p + i] = v[p];
+    }
+#pragma unroll
+    for (int h = H0; h < RAD; h <<= 1) {
 #pragma unroll
         for (int s = 0; s < RAD; s += 2 * h) {
 #pragma unroll
@@ -103,8 +114,13 @@ __device__ __forceinline__ void dft_reg(float2 *v) {
 // (Ns = product of the radices of the earlier passes).  Each of the T = n/16
 // threads of the row owns 16 values: 16/RAD butterflies j = tid + g T.
 // FIRST: the pass reads the windowed beat samples from global memory.
-// STAGED: the beat row, the window and the twiddles are in shared memory.
-template <int RAD, int SGN, bool FIRST, bool STAGED = false>
+// STAGED: the beat row, the window and the twiddles are in shared memory;
+// there tw is this pass's own table: for each power 2^i < RAD the Ns
+// twiddles exp(SGN j 2 pi k 2^i / (Ns RAD)), k < Ns (consecutive threads read
+// consecutive entries).  Otherwise tw is the full N_fft-point table.
+// ZR (first pass): N_fft / N = 16 / ZR, so only the first ZR of a thread's
+// 16 inputs lie inside the chirp; the rest are the zero padding.
+template <int RAD, int SGN, bool FIRST, bool STAGED = false, int ZR = RAD>
 __device__ __forceinline__ void stockham_pass(float2 *X, int n, int log2n, int Ns, int tid, int T,
                                               bool active, const float2 *__restrict__ tw,
                                               const float2 *__restrict__ beat_row,
@@ -120,7 +136,7 @@ __device__ __forceinline__ void stockham_pass(float2 *X, int n, int log2n, int N
             const int idx = j + r * stride;
             if (FIRST) {
                 float2 x = make_float2(0.f, 0.f);
-                if (active && idx < N) {
+                if (active && r < ZR && (ZR < RAD || idx < N)) {
                     const float2 b = STAGED ? beat_row[idx] : __ldg(beat_row + idx);
                     const float w = STAGED ? w_r[idx] : __ldg(w_r + idx);
                     x = make_float2(w * b.x, w * b.y);
@@ -142,11 +158,18 @@ __device__ __forceinline__ void stockham_pass(float2 *X, int n, int log2n, int N
             // w^r for r < RAD from the loaded powers w, w^2, w^4, w^8 (at most
             // three complex products deep: ~4e-7 relative error)
             float2 wp[16];
-            const int t1 = k << tw_shift;
-            wp[1] = STAGED ? tw[t1] : __ldg(tw + t1);
-            if (RAD > 2) wp[2] = STAGED ? tw[2 * t1] : __ldg(tw + 2 * t1);
-            if (RAD > 4) wp[4] = STAGED ? tw[4 * t1] : __ldg(tw + 4 * t1);
-            if (RAD > 8) wp[8] = STAGED ? tw[8 * t1] : __ldg(tw + 8 * t1);
+            if (STAGED) {
+                wp[1] = tw[k];
+                if (RAD > 2) wp[2] = tw[Ns + k];
+                if (RAD > 4) wp[4] = tw[2 * Ns + k];
+                if (RAD > 8) wp[8] = tw[3 * Ns + k];
+            } else {
+                const int t1 = k << tw_shift;
+                wp[1] = __ldg(tw + t1);
+                if (RAD > 2) wp[2] = __ldg(tw + 2 * t1);
+                if (RAD > 4) wp[4] = __ldg(tw + 4 * t1);
+                if (RAD > 8) wp[8] = __ldg(tw + 8 * t1);
+            }
             if (RAD > 2) wp[3] = cmul(wp[1], wp[2]);
             if (RAD > 4) {
                 wp[5] = cmul(wp[4], wp[1]);
@@ -160,7 +183,7 @@ __device__ __forceinline__ void stockham_pass(float2 *X, int n, int log2n, int N
 #pragma unroll
             for (int r = 1; r < RAD; ++r) v[g * RAD + r] = cmul(v[g * RAD + r], wp[r]);
         }
-        dft_reg<RAD, SGN>(v + g * RAD);
+        dft_reg<RAD, SGN, FIRST ? ZR : RAD>(v + g * RAD);
         const int base = (j - k) * RAD + k;
 #pragma unroll
         for (int r = 0; r < RAD; ++r) X[pad16(base + r * Ns)] = v[g * RAD + r];
@@ -293,13 +316,18 @@ __device__ __forceinline__ void store_row(const RcArgs &a, const float2 *X, long
     }
 }
 
+// Start of the twiddle table of the pass with Ns = 16^q (q >= 1) in the
+// per-pass tables of the persistent kernel: 4 (16 + 256 + ... + 16^(q-1)).
+__host__ __device__ constexpr int pass_table_offset(int q) { return 4 * (((1 << (4 * q)) - 16) / 15); }
+
 // Persistent form for N_fft <= 4096 (256 threads, 4096 / N_fft rows per
-// group).  Twiddles and window sit in shared memory for the CTA's lifetime;
-// the beat samples of the next row group are copied in with cp.async while
-// the current group is transformed.  LOGN > 0: N_fft = 2^LOGN fixed at
-// compile time (index and twiddle arithmetic folds into constants); 0: any
-// size.
-template <int SGN, int MODE, int LOGN>
+// group).  Per-pass twiddle tables and the window sit in shared memory for
+// the CTA's lifetime; the beat samples of the next row group are copied in
+// with cp.async while the current group is transformed.  LOGN > 0: N_fft =
+// 2^LOGN fixed at compile time (index and twiddle arithmetic folds into
+// constants); 0: any size.  ZR < 16: N_fft = 16 N / ZR, and the first pass
+// skips the zero padding.
+template <int SGN, int MODE, int LOGN, int ZR>
 __global__ void __launch_bounds__(256, 2) range_compress_persistent(RcArgs a, long long n_groups) {
     extern __shared__ float2 smem_rcp[];
     __shared__ int row_max[64];
@@ -313,7 +341,20 @@ __global__ void __launch_bounds__(256, 2) range_compress_persistent(RcArgs a, lo
     float2 *tw = smem_rcp + (size_t)rows_per * (n + n / 16);
     float2 *stage = tw + n;  // [2][rows_per][N]
     float *wr = reinterpret_cast<float *>(stage + 2 * rows_per * N);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = __ldg(a.tw + i);
+    // per-pass twiddle tables (at most N_fft / 2 entries): the pass with Ns
+    // and radix RAD holds tw[(k << i) N_fft / (Ns RAD)] at i Ns + k
+    {
+        const int n16 = log2n >> 2, rem = log2n & 3;
+        for (int q = 1; q <= n16; ++q) {
+            const int lns = 4 * q, Ns = 1 << lns;
+            const int lrad = q < n16 ? 4 : rem;
+            if (lrad == 0) break;
+            const int step = n >> (lns + lrad);
+            float2 *dst = tw + pass_table_offset(q);
+            for (int i = threadIdx.x; i < lrad * Ns; i += blockDim.x)
+                dst[i] = __ldg(a.tw + (((i & (Ns - 1)) << (i >> lns)) * step));
+        }
+    }
     for (int i = threadIdx.x; i < N; i += blockDim.x) wr[i] = __ldg(a.w_r + i);
     const uint32_t stage_addr = (uint32_t)__cvta_generic_to_shared(stage);
     const int per_group = rows_per * N;
@@ -362,23 +403,23 @@ __global__ void __launch_bounds__(256, 2) range_compress_persistent(RcArgs a, lo
         const float2 *src = stage + (size_t)((it & 1) * rows_per + lrow) * N;
         const int n16 = log2n >> 2;
         const int rem = log2n & 3;
-        stockham_pass<16, SGN, true, true>(X, n, log2n, 1, tid, T, active, tw, src, wr, N);
-        int Ns = 16;
+        stockham_pass<16, SGN, true, true, ZR>(X, n, log2n, 1, tid, T, active, tw, src, wr, N);
         if (LOGN) {
 #pragma unroll
             for (int p = 1; p < (LOGN >> 2); ++p) {
-                stockham_pass<16, SGN, false, true>(X, n, log2n, 1 << (4 * p), tid, T, active, tw, src, wr, N);
+                stockham_pass<16, SGN, false, true>(X, n, log2n, 1 << (4 * p), tid, T, active,
+                                                    tw + pass_table_offset(p), src, wr, N);
             }
-            Ns = 1 << (4 * (LOGN >> 2));
         } else {
-            for (int p = 1; p < n16; ++p) {
-                stockham_pass<16, SGN, false, true>(X, n, log2n, Ns, tid, T, active, tw, src, wr, N);
-                Ns <<= 4;
-            }
+            for (int p = 1; p < n16; ++p)
+                stockham_pass<16, SGN, false, true>(X, n, log2n, 1 << (4 * p), tid, T, active,
+                                                    tw + pass_table_offset(p), src, wr, N);
         }
-        if (rem == 1) stockham_pass<2, SGN, false, true>(X, n, log2n, Ns, tid, T, active, tw, src, wr, N);
-        if (rem == 2) stockham_pass<4, SGN, false, true>(X, n, log2n, Ns, tid, T, active, tw, src, wr, N);
-        if (rem == 3) stockham_pass<8, SGN, false, true>(X, n, log2n, Ns, tid, T, active, tw, src, wr, N);
+        const int Ns = 1 << (4 * n16);
+        const float2 *twr = tw + pass_table_offset(n16);
+        if (rem == 1) stockham_pass<2, SGN, false, true>(X, n, log2n, Ns, tid, T, active, twr, src, wr, N);
+        if (rem == 2) stockham_pass<4, SGN, false, true>(X, n, log2n, Ns, tid, T, active, twr, src, wr, N);
+        if (rem == 3) stockham_pass<8, SGN, false, true>(X, n, log2n, Ns, tid, T, active, twr, src, wr, N);
         store_row<MODE>(a, X, row, active, tid, T, lrow, row_max);
         __syncthreads();  // X and this group's stage buffer are reused next
     }
@@ -393,9 +434,12 @@ cudaError_t launch_rc(const RcArgs &a, cudaStream_t s) {
         if (n_groups == 0) return cudaSuccess;
         const size_t smem = ((size_t)rows_per * (n + n / 16) + n + 2 * (size_t)rows_per * a.N) * sizeof(float2) +
                             (size_t)a.N * sizeof(float);
-        auto kern = n == 4096   ? range_compress_persistent<SGN, MODE, 12>
-                    : n == 2048 ? range_compress_persistent<SGN, MODE, 11>
-                                : range_compress_persistent<SGN, MODE, 0>;
+        const bool os4 = n == 4 * a.N;
+        auto kern = n == 4096   ? (os4 ? range_compress_persistent<SGN, MODE, 12, 4>
+                                       : range_compress_persistent<SGN, MODE, 12, 16>)
+                    : n == 2048 ? (os4 ? range_compress_persistent<SGN, MODE, 11, 4>
+                                       : range_compress_persistent<SGN, MODE, 11, 16>)
+                                : range_compress_persistent<SGN, MODE, 0, 16>;
         int dev = 0, sms = 0, optin = 0, occ = 0;
         cudaFuncAttributes fa;
         if (cudaGetDevice(&dev) != cudaSuccess ||
