@@ -246,19 +246,44 @@ def make_workload(name: str, seed: int = 0) -> Workload:
 def beat_signal(radar: Radar, q_tx: np.ndarray, q_rx: np.ndarray,
                 targets: np.ndarray, amps: np.ndarray, rvp: bool = False,
                 snr_db: Optional[float] = None, seed: int = 0,
-                device: Optional[str] = None, chunk: int = 64) -> np.ndarray:
+                device: Optional[str] = None, chunk: int = 64,
+                intra_chirp_velocity: Optional[np.ndarray] = None) -> np.ndarray:
     """Stop-and-hop FMCW beat cube [M, R, N] (complex128, numpy).
 
     ``device`` = None computes with numpy on the CPU; a torch device string
     ("cuda") computes the same FP64 formula with torch (for large scenes).
     AWGN (if ``snr_db``) is per-sample, relative to the mean power of the
     noiseless cube, drawn from PCG64(seed + 1).
+
+    ``intra_chirp_velocity`` ([2] or [M, 2], m/s; numpy path only) drops the
+    stop-and-hop assumption: during chirp m every antenna moves from its
+    chirp-start position at that velocity, so the delay is re-evaluated at
+    every sample, ``tau(t) = (|p - q_tx - v t| + |p - q_rx - v t|) / c``, and
+    the phase is ``f0 tau(t) + mu tau(t) t``.  Its rate of change is the
+    Doppler shift that Alg. 1's velocity term compensates.
     """
     M = q_tx.shape[0]
     R = q_rx.shape[1]
     N = radar.n_samples
     t = np.arange(N, dtype=np.float64) / radar.fs
-    if device is None:
+    if intra_chirp_velocity is not None:
+        if device is not None:
+            raise ValueError("intra_chirp_velocity is computed on the numpy path only")
+        v = np.broadcast_to(np.asarray(intra_chirp_velocity, dtype=np.float64), (M, 2))
+        out = np.zeros((M, R, N), dtype=np.complex128)
+        for k, (p, a) in enumerate(zip(targets, amps)):
+            # antenna positions at every sample: [M, N, 2] and [M, R, N, 2]
+            tx = q_tx[:, None, :] + v[:, None, :] * t[None, :, None]
+            rx = q_rx[:, :, None, :] + v[:, None, None, :] * t[None, None, :, None]
+            dtx = np.hypot(p[0] - tx[..., 0], p[1] - tx[..., 1])             # [M, N]
+            drx = np.hypot(p[0] - rx[..., 0], p[1] - rx[..., 1])             # [M, R, N]
+            tau = (dtx[:, None, :] + drx) / radar.c                          # [M, R, N]
+            ph = radar.f0 * tau
+            if rvp:
+                ph = ph - 0.5 * radar.slope * tau * tau
+            ph = ph - np.floor(ph) + radar.slope * tau * t
+            out += a * np.exp(-2j * np.pi * ph)
+    elif device is None:
         out = np.zeros((M, R, N), dtype=np.complex128)
         for k0 in range(0, len(targets), chunk):
             tk = targets[k0:k0 + chunk]

@@ -49,6 +49,10 @@ MUTANTS = [
      "if (!(fl >= crop_lo && fl <= crop_hi)) return 0;", None),
     ("alg1_f0_dropped", "const double ph = sign * 2.0 * PI * f0 * tau;",
      "const double ph = sign * 2.0 * PI * tau;", None),
+    ("alg1_doppler_sign", "const double f_hyp = slope * tau + f0 * (v_tx + v_rx) / c;",
+     "const double f_hyp = slope * tau - f0 * (v_tx + v_rx) / c;", None),
+    ("alg1_rx_velocity_dropped", "const double f_hyp = slope * tau + f0 * (v_tx + v_rx) / c;",
+     "const double f_hyp = slope * tau + f0 * v_tx / c;", None),
     ("mf_frequency_scale", "const double cyc = slope * d / (c * fs);",
      "const double cyc = slope * d / (c * fs) * 1.01;", None),
     ("mf_phase_sign", "ph *= sign * 2.0 * PI;", "ph *= -sign * 2.0 * PI;", None),
