@@ -46,7 +46,7 @@ def _bind(lib):
     lib.oracle_window.argtypes = [i, i, d, dp]
     lib.oracle_dft.argtypes = [i, dp, i, i, dp]
     lib.oracle_fft.argtypes = [i, dp, i]
-    lib.oracle_range_compress.argtypes = [i, i, i, i, dp, dp, i, dp, i]
+    lib.oracle_range_compress.argtypes = [i, i, i, i, dp, dp, i, d, dp, i]
     lib.oracle_backproject.argtypes = [d, d, d, d, i, i, i, i, i, i, dp, dp, dp,
                                        dp, dp, i, dp, dp, i]
     lib.oracle_backproject_alg1.argtypes = [d, d, d, d, i, i, i, i, i, i, dp, dp,
@@ -114,28 +114,38 @@ def fft(x, sign: int = 1, lib=None) -> np.ndarray:
 
 
 def range_compress(beat, w_r, os_factor: int, sign: int = 1, threads: int = 0,
-                   lib=None) -> np.ndarray:
-    """beat [M, R, N] -> S [M, R, N * os]."""
+                   lib=None, t0: float = 0.0) -> np.ndarray:
+    """beat [M, R, N] -> S [M, R, N * os], transform time origin t0 samples."""
     lib = lib or load()
     beat = _c128(beat)
     M, R, N = beat.shape
     S = np.empty((M, R, N * os_factor), np.complex128)
     _check(lib.oracle_range_compress(N, os_factor, M, R, _ptr(beat.view(np.float64)),
-                                     _ptr(_f64(w_r)), sign, _ptr(S.view(np.float64)),
-                                     threads), "oracle_range_compress")
+                                     _ptr(_f64(w_r)), sign, float(t0),
+                                     _ptr(S.view(np.float64)), threads),
+           "oracle_range_compress")
     return S
 
 
+def carrier_at(radar, t0: float) -> float:
+    """The frequency at time t0 / fs into the chirp, f0 + mu t0 / fs: the
+    beat phase f0 tau + mu tau t of Sec. II, with its time origin moved to
+    sample t0, has this as its constant-phase coefficient."""
+    return radar.f0 + radar.slope * t0 / radar.fs
+
+
 def backproject(radar, S, q_tx, q_rx, px, w_az=None, fd_idx=None, sign: int = 1,
-                crop=None, threads: int = 0, lib=None) -> np.ndarray:
-    """Alg. 2 on the pixel list px [P, 2]; returns complex128 [P]."""
+                crop=None, threads: int = 0, lib=None, t0: float = 0.0) -> np.ndarray:
+    """Alg. 2 on the pixel list px [P, 2]; returns complex128 [P].  S must come
+    from a range transform with time origin t0 (samples); the phase then uses
+    the carrier at that origin."""
     lib = lib or load()
     S = _c128(S)
     M, R, nfft = S.shape
     lo, hi = crop if crop is not None else (0, nfft - 1)
     px = _f64(px).reshape(-1, 2)
     out = np.empty(len(px), np.complex128)
-    _check(lib.oracle_backproject(radar.f0, radar.slope, radar.fs, radar.c, nfft, sign,
+    _check(lib.oracle_backproject(carrier_at(radar, t0), radar.slope, radar.fs, radar.c, nfft, sign,
                                   lo, hi, M, R, _ptr(S.view(np.float64)),
                                   _ptr(_f64(q_tx)), _ptr(_f64(q_rx)), _ptr(_f64(w_az)),
                                   _ptr(_f64(fd_idx)), len(px), _ptr(px),
@@ -183,12 +193,12 @@ def threads(lib=None) -> int:
 
 
 def form_image(wl, beat, w_az=None, range_window: int = WINDOW_HANN, sign: int = 1,
-               px=None, crop=None, threads: int = 0):
+               px=None, crop=None, threads: int = 0, t0: float = 0.0):
     """Range compression then Alg. 2 for a synth.Workload (convenience)."""
     r = wl.radar
     w_r = window(range_window, r.n_samples)
-    S = range_compress(beat, w_r, r.os, sign=sign, threads=threads)
+    S = range_compress(beat, w_r, r.os, sign=sign, threads=threads, t0=t0)
     if px is None:
         px = wl.grid.pixels()
     return backproject(r, S, wl.q_tx, wl.q_rx, px, w_az=w_az, sign=sign,
-                       crop=crop if crop is not None else wl.crop, threads=threads)
+                       crop=crop if crop is not None else wl.crop, threads=threads, t0=t0)

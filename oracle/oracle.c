@@ -140,13 +140,18 @@ API int oracle_fft(int n, double *x, int sign) {
 /*
  * Range compression of every (chirp m, Rx r) row of the beat cube
  * beat[M][R][N]: window by w_r[n], zero-pad to N_fft = os * N and transform,
- * S[m][r][k] = sum_{n < N} w_r[n] beat[m][r][n] exp(sign j 2 pi n k / N_fft)
+ * S[m][r][k] = sum_{n < N} w_r[n] beat[m][r][n] exp(sign j 2 pi (n - t0) k / N_fft)
  * for k < N_fft.  The paper interpolates the beat spectrum "at f_hyp"
  * (Alg. 1) on an equidistant beat-frequency axis (Sec. III-C) without saying
  * how it is made; this is the windowed, zero-padded DFT of each chirp.
+ * t0 is the transform's time origin in samples: 0 (the chirp's first sample,
+ * the default reading of Sec. II's f0) or (N - 1) / 2 (the chirp centre).
+ * The transform is computed for n and then moved to n - t0 by the shift
+ * theorem, one rotation exp(-sign j 2 pi t0 k / N_fft) per bin.
  */
 API int oracle_range_compress(int N, int os, int M, int R, const double *beat,
-                              const double *w_r, int sign, double *S, int threads) {
+                              const double *w_r, int sign, double t0, double *S,
+                              int threads) {
     if (N <= 0 || os <= 0 || M < 0 || R <= 0) return -1;
     int nfft = N * os;
     if (nfft & (nfft - 1)) return -1;
@@ -163,6 +168,15 @@ API int oracle_range_compress(int N, int os, int M, int R, const double *beat,
             out[2 * n + 1] = w_r[n] * in[2 * n + 1];
         }
         err |= oracle_fft(nfft, out, sign);
+        if (t0 != 0.0) {
+            for (int k = 0; k < nfft; ++k) {
+                const double ang = -sign * 2.0 * PI * t0 * k / nfft;
+                const double cr = cos(ang), ci = sin(ang);
+                const double re = out[2 * k], im = out[2 * k + 1];
+                out[2 * k] = re * cr - im * ci;
+                out[2 * k + 1] = re * ci + im * cr;
+            }
+        }
     }
     return err ? -1 : 0;
 }

@@ -77,6 +77,12 @@ def pin_range_compress(lib):
     assert np.allclose(S, ref, atol=1e-10)
     Sm = oracle.range_compress(beat, w, os_, -1, lib=lib)
     assert np.allclose(Sm, np.einsum("kn,mrn->mrk", E.conj(), beat * w), atol=1e-10)
+    # time origin at the chirp centre: the DFT over the centred index n - t0
+    t0 = (N - 1) / 2.0
+    Ec = np.exp(2j * np.pi * (n - t0) * k / (N * os_))
+    for sg, Es in ((+1, Ec), (-1, Ec.conj())):
+        Sc = oracle.range_compress(beat, w, os_, sg, lib=lib, t0=t0)
+        assert np.allclose(Sc, np.einsum("kn,mrn->mrk", Es, beat * w), atol=1e-10)
 
 
 # --------------------------------------------------------------------------
@@ -132,6 +138,32 @@ def pin_backproject_point_target(lib):
     assert int(np.argmax(np.abs(img))) == 4 * 9 + 4
 
 
+def pin_time_origin_mid_bin(lib):
+    """One term whose index falls exactly half-way between two bins (one chirp,
+    Rx at the Tx, range-window Hann).  With the transform's time origin at the
+    chirp centre, the windowed tone's spectrum is real around its peak, so the
+    interpolated magnitude is the window transform half a bin off,
+    C = sum_n w[n] cos(pi (n - (N-1)/2) / N_fft), and the image phase is arg(a).
+    With the origin at sample 0 the two neighbours differ in phase by
+    pi (N-1) / N_fft, and interpolation loses cos(pi (N-1) / (2 N_fft)) more."""
+    radar = _radar(n_rx=1, os=4)
+    N, nfft = radar.n_samples, radar.n_fft
+    w = np.hanning(N)
+    a = 0.9 * np.exp(0.4j)
+    d = (100.5) / radar.bins_per_metre            # two-way path on a mid-bin index
+    q_tx = np.array([[0.0, 0.0]])
+    q_rx = np.array([[[0.0, 0.0]]])
+    tgt = np.array([[0.0, d / 2.0]])
+    beat = synth.beat_signal(radar, q_tx, q_rx, tgt, np.array([a]))
+    t0 = (N - 1) / 2.0
+    C = abs(np.sum(w * np.cos(np.pi * (np.arange(N) - t0) / nfft)))
+    for origin, expect in ((t0, C), (0.0, C * math.cos(np.pi * (N - 1) / (2.0 * nfft)))):
+        S = oracle.range_compress(beat, w, radar.os, lib=lib, t0=origin)
+        P = oracle.backproject(radar, S, q_tx, q_rx, tgt, lib=lib, t0=origin)[0]
+        assert abs(abs(P) - abs(a) * expect) < 1e-9 * abs(a) * C, (origin, abs(P), expect)
+        assert abs(np.angle(P / a)) < 1e-9
+
+
 def pin_interpolation_convergence(lib):
     """FFT + lerp converges to the brute-force matched filter as the
     zero-padding factor grows: linear interpolation is second order, so the
@@ -141,7 +173,7 @@ def pin_interpolation_convergence(lib):
     tg = np.stack([rng.uniform(-0.5, 0.5, 3), rng.uniform(2.5, 3.5, 3)], 1)
     am = rng.standard_normal(3) + 1j * rng.standard_normal(3)
     g = synth.Grid(x0=-0.6, y0=2.4, dx=0.1, dy=0.1, nx=13, ny=13)
-    errs = []
+    errs, errs_c = [], []
     for os_ in (4, 8, 16):
         radar = _radar(os=os_)
         q_tx, q_rx = synth.trajectory(radar, M)
@@ -151,8 +183,16 @@ def pin_interpolation_convergence(lib):
         S = oracle.range_compress(beat, w_r, os_, lib=lib)
         img = oracle.backproject(radar, S, q_tx, q_rx, g.pixels(), lib=lib)
         errs.append(rel_l2(img, ref))
+        # the same limit with the transform's time origin at the chirp centre,
+        # where the spectrum's phase is flat across the main lobe
+        t0 = (radar.n_samples - 1) / 2.0
+        S = oracle.range_compress(beat, w_r, os_, lib=lib, t0=t0)
+        img = oracle.backproject(radar, S, q_tx, q_rx, g.pixels(), lib=lib, t0=t0)
+        errs_c.append(rel_l2(img, ref))
     assert errs[0] < 0.1, errs
     assert errs[1] / errs[0] < 0.35 and errs[2] / errs[1] < 0.35, errs
+    assert errs_c[1] / errs_c[0] < 0.35 and errs_c[2] / errs_c[1] < 0.35, errs_c
+    assert all(c < 0.2 * e for c, e in zip(errs_c, errs)), (errs_c, errs)
 
 
 def _minus3db_width(coord, mag):
@@ -372,7 +412,8 @@ def pin_bp_matches_matched_filter(lib):
 
 ALL_PINS = [
     pin_fft, pin_windows, pin_range_compress, pin_matched_filter_closed_form,
-    pin_backproject_point_target, pin_interpolation_convergence, pin_resolution,
+    pin_backproject_point_target, pin_time_origin_mid_bin, pin_interpolation_convergence,
+    pin_resolution,
     pin_linearity, pin_alg1_equals_alg2, pin_alg1_doppler_sign, pin_rx_halving, pin_single_term,
     pin_subaperture_additivity, pin_translation_invariance,
     pin_bp_matches_matched_filter,

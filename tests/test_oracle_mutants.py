@@ -53,6 +53,8 @@ MUTANTS = [
      "const double f_hyp = slope * tau - f0 * (v_tx + v_rx) / c;", None),
     ("alg1_rx_velocity_dropped", "const double f_hyp = slope * tau + f0 * (v_tx + v_rx) / c;",
      "const double f_hyp = slope * tau + f0 * v_tx / c;", None),
+    ("time_origin_rotation_sign", "const double ang = -sign * 2.0 * PI * t0 * k / nfft;",
+     "const double ang = sign * 2.0 * PI * t0 * k / nfft;", None),
     ("mf_frequency_scale", "const double cyc = slope * d / (c * fs);",
      "const double cyc = slope * d / (c * fs) * 1.01;", None),
     ("mf_phase_sign", "ph *= sign * 2.0 * PI;", "ph *= -sign * 2.0 * PI;", None),
