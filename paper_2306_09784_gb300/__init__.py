@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libsar.so")
  SAR_ESCRATCH) = range(9)
 WINDOW_RECT, WINDOW_HANN, WINDOW_KAISER = 0, 1, 2
 PREC_FP32, PREC_FP16 = 0, 1
+ORIGIN_FIRST_SAMPLE, ORIGIN_CHIRP_CENTRE = 0, 1
 
 # Every symbol include/sar.h declares (checked by the tests).
 EXPORTS = (
@@ -48,7 +49,7 @@ class RadarParams(ctypes.Structure):
         ("range_window", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("kaiser_beta", ctypes.c_double), ("phase_sign", ctypes.c_int32),
         ("crop_lo", ctypes.c_int32), ("crop_hi", ctypes.c_int32),
-        ("reserved", ctypes.c_int32), ("max_doppler_bins", ctypes.c_double),
+        ("time_origin", ctypes.c_int32), ("max_doppler_bins", ctypes.c_double),
     ]
 
 
@@ -187,14 +188,15 @@ class Plan:
                  os_factor: int, n_rx: int, max_pulses: int, grid=None, pixels_xy=None,
                  range_window: int = WINDOW_HANN, precision: int = PREC_FP32,
                  kaiser_beta: float = 6.0, phase_sign: int = 1, crop=(0, 0),
-                 max_doppler_bins: float = 0.0, hbm_budget: int = 0):
+                 max_doppler_bins: float = 0.0, hbm_budget: int = 0,
+                 time_origin: int = ORIGIN_FIRST_SAMPLE):
         self._lib = load_library()
         self._plan = None
         p = RadarParams(f0=f0, slope=slope, fs=fs, c=c, n_samples=n_samples, os=os_factor,
                         n_rx=n_rx, max_pulses=max_pulses, range_window=range_window,
                         precision=precision, kaiser_beta=kaiser_beta, phase_sign=phase_sign,
-                        crop_lo=int(crop[0]), crop_hi=int(crop[1]), reserved=0,
-                        max_doppler_bins=max_doppler_bins)
+                        crop_lo=int(crop[0]), crop_hi=int(crop[1]),
+                        time_origin=int(time_origin), max_doppler_bins=max_doppler_bins)
         g = Grid()
         self._pix_keep = None
         if pixels_xy is not None:

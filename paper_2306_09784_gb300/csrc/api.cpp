@@ -29,6 +29,7 @@ struct sar_plan {
     int device = 0;
     int n_fft = 0, log2n = 0, crop_lo = 0, crop_hi = 0, n_bins = 0;
     double a1 = 0, beta = 0;
+    double beta_frac = 0;  // cycles per bin of the interpolated fraction (beta at the time origin)
     int sign = 1;
     bool fp16 = false;
     int64_t n_pixels = 0;
@@ -412,6 +413,8 @@ int validate_params(const sar_radar_params *p) {
         if (p->crop_lo >= p->crop_hi || p->crop_hi > nfft - 1) return SAR_EINVAL;
     }
     if (!(p->max_doppler_bins >= 0) || p->max_doppler_bins > 64) return SAR_EINVAL;
+    if (p->time_origin != SAR_ORIGIN_FIRST_SAMPLE && p->time_origin != SAR_ORIGIN_CHIRP_CENTRE)
+        return SAR_EINVAL;
     if (p->range_window == SAR_WINDOW_KAISER && !(p->kaiser_beta >= 0 && p->kaiser_beta < 100)) return SAR_EINVAL;
     // bins per metre a1 and phase cycles per bin beta (the kernels scale by
     // 2 pi beta and by its inverse)
@@ -444,6 +447,15 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
     pl->fp16 = p.precision == SAR_PREC_FP16;
     pl->a1 = p.slope * pl->n_fft / (p.c * p.fs);  // validated positive
     pl->beta = p.f0 / (p.c * pl->a1);              // validated in [1e-9, 1e9]
+    // A transform whose time origin is sample t0 has the carrier f0 + slope
+    // t0 / fs, i.e. beta + t0 / N_fft cycles per bin, and its bin k equals the
+    // first-sample transform's times exp(-sign j 2 pi t0 k / N_fft).  That
+    // rotation and the one by beta combine into the per-bin rotation by beta
+    // the range compression already stores, so only the backprojection's
+    // fractional-phase rate changes.
+    pl->beta_frac = pl->beta;
+    if (p.time_origin == SAR_ORIGIN_CHIRP_CENTRE)
+        pl->beta_frac += 0.5 * (double)(p.n_samples - 1) / (double)pl->n_fft;
     pl->fd_max = (float)p.max_doppler_bins;
 
     HostTiles ht;
@@ -623,17 +635,17 @@ BpArgs common_bp_args(const sar_plan *pl, const void *prof, int M, const double 
     a.accumulate = accumulate ? 1 : 0;
     a.a1 = pl->a1;
     a.a1f = (float)pl->a1;
-    // kappa = sign 2 pi beta rounded to 22 significant bits, so that
+    // kappa = sign 2 pi beta_frac rounded to 22 significant bits, so that
     // kappa * 1.5 * 2^23 is exact in FP32 (the kernel's fractional-phase step
     // relies on it); the relative change is below 2.4e-7.
     int ex = 0;
-    const double mant = std::frexp(pl->sign * 2.0 * kPi * pl->beta, &ex);
+    const double mant = std::frexp(pl->sign * 2.0 * kPi * pl->beta_frac, &ex);
     const float kap = (float)std::ldexp(std::nearbyint(std::ldexp(mant, 22)), ex - 22);
     a.kappa = kap;
     a.kappa_magic = (float)((double)kap * 12582912.0);
-    a.beta = (float)pl->beta;
+    a.beta = (float)pl->beta_frac;
     a.sign = (float)pl->sign;
-    const double cb = -pl->sign * 2.0 * kPi * (pl->beta - std::floor(pl->beta));
+    const double cb = -pl->sign * 2.0 * kPi * (pl->beta_frac - std::floor(pl->beta_frac));
     a.cb_k = make_float2((float)(std::cos(cb) / kap), (float)(std::sin(cb) / kap));
     a.inv_kappa = (float)(1.0 / kap);
     a.fd_max = pl->fd_max;

@@ -74,12 +74,13 @@ struct BpArgs {
     int accumulate;
     double a1;                 // bins per metre
     float a1f;
-    float kappa;               // sign * 2 pi beta (radians per bin), 22 significant bits
+    float kappa;               // sign * 2 pi beta' (radians per bin), 22 significant bits;
+                               // beta' = cycles per bin at the transform's time origin
     float kappa_magic;         // kappa * 1.5 * 2^23 (exact)
     float inv_kappa;           // 1 / kappa
-    float beta;                // cycles per bin
+    float beta;                // beta' (cycles per bin at the time origin)
     float sign;
-    float2 cb_k;               // exp(-sign j 2 pi beta) / kappa
+    float2 cb_k;               // exp(-sign j 2 pi beta') / kappa
     float fd_max;              // bound on |f_doppler|
     unsigned long long div_nq; // ceil(2^32 / (L / 4)): division by the groups per window
     unsigned long long div_r;  // ceil(2^32 / R)

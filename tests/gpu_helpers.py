@@ -51,15 +51,15 @@ def gpu_image(plan, wl, beat, w_az, M=None, fdopp=None):
 
 
 def oracle_image(wl, beat, w_az, px=None, crop=None, sign=1, fd_idx=None, range_window=1,
-                 threads=0):
+                 threads=0, t0=0.0):
     r = wl.radar
     w_r = oracle.window(range_window, r.n_samples)
-    S = oracle.range_compress(beat, w_r, r.os, sign=sign, threads=threads)
+    S = oracle.range_compress(beat, w_r, r.os, sign=sign, threads=threads, t0=t0)
     if px is None:
         px = wl.grid.pixels()
     return oracle.backproject(r, S, wl.q_tx, wl.q_rx, px, w_az=w_az, sign=sign,
                               fd_idx=fd_idx, crop=crop if crop is not None else wl.crop,
-                              threads=threads)
+                              threads=threads, t0=t0)
 
 
 def nearest_pixel(grid, pt):

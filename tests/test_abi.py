@@ -76,7 +76,7 @@ def test_plan_parameters_rejected_without_gpu(lib):
     def params(**kw):
         p = dict(f0=77e9, slope=1e9 / 102.4e-6, fs=128 / 102.4e-6, c=299792458.0, n_samples=128,
                  os=4, n_rx=4, max_pulses=64, range_window=1, precision=0, kaiser_beta=0.0,
-                 phase_sign=1, crop_lo=0, crop_hi=0, reserved=0, max_doppler_bins=0.0)
+                 phase_sign=1, crop_lo=0, crop_hi=0, time_origin=0, max_doppler_bins=0.0)
         p.update(kw)
         return sar.RadarParams(**p)
 
@@ -86,7 +86,7 @@ def test_plan_parameters_rejected_without_gpu(lib):
            dict(n_samples=8, os=4), dict(n_samples=8192, os=4), dict(range_window=3),
            dict(precision=2), dict(phase_sign=0), dict(crop_lo=10, crop_hi=5),
            dict(crop_lo=0, crop_hi=512), dict(max_doppler_bins=-1.0), dict(max_doppler_bins=100.0),
-           dict(range_window=2, kaiser_beta=-1.0),
+           dict(range_window=2, kaiser_beta=-1.0), dict(time_origin=2), dict(time_origin=-1),
            dict(f0=1e-6),      # beta = f0 / (c a1) ~ 2.5e-15 cycles per bin
            dict(f0=1e19),      # beta ~ 2.5e9
            dict(slope=-1e9 / 102.4e-6)]  # a1 < 0
@@ -110,7 +110,8 @@ def test_struct_layouts_match_header():
 int main(void) {
   printf("sar_radar_params %zu\nsar_grid %zu\nsar_plan_info %zu\n",
          sizeof(sar_radar_params), sizeof(sar_grid), sizeof(sar_plan_info));
-  P(sar_radar_params, kaiser_beta) P(sar_radar_params, phase_sign) P(sar_radar_params, max_doppler_bins)
+  P(sar_radar_params, kaiser_beta) P(sar_radar_params, phase_sign) P(sar_radar_params, time_origin)
+  P(sar_radar_params, max_doppler_bins)
   P(sar_grid, pixels_xy) P(sar_grid, n_pixels)
   P(sar_plan_info, n_pixels) P(sar_plan_info, bins_per_metre) P(sar_plan_info, device_bytes)
   P(sar_plan_info, rx_group) P(sar_plan_info, regs_ctas_per_sm)
@@ -133,6 +134,7 @@ int main(void) {
     assert int(got["sar_plan_info"]) == ctypes.sizeof(sar.PlanInfo)
     assert int(got["sar_radar_params.kaiser_beta"]) == sar.RadarParams.kaiser_beta.offset
     assert int(got["sar_radar_params.phase_sign"]) == sar.RadarParams.phase_sign.offset
+    assert int(got["sar_radar_params.time_origin"]) == sar.RadarParams.time_origin.offset
     assert int(got["sar_radar_params.max_doppler_bins"]) == sar.RadarParams.max_doppler_bins.offset
     assert int(got["sar_grid.pixels_xy"]) == sar.Grid.pixels_xy.offset
     assert int(got["sar_grid.n_pixels"]) == sar.Grid.n_pixels.offset

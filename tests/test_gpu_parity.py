@@ -348,6 +348,30 @@ def test_doppler_offsets_at_the_largest_bound(torch, small):
     assert rel_l2(img, ref) <= TOL_FP32
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_time_origin_chirp_centre(torch, small, precision):
+    """Transform time origin at the chirp centre: the CUDA image equals the
+    oracle's centred-transform image (carrier at the centre instant), with and
+    without Doppler offsets; it differs from the first-sample image by the
+    interpolation error that the centring removes."""
+    import paper_2306_09784_gb300 as sar
+    wl, beat, w_az = small
+    t0 = (wl.radar.n_samples - 1) / 2.0
+    tol = TOL_FP32 if precision == 0 else TOL_FP16
+    plan = make_plan(wl, precision=precision, time_origin=sar.ORIGIN_CHIRP_CENTRE,
+                     max_doppler_bins=2.0)
+    img = gpu_image(plan, wl, beat, w_az)
+    ref = oracle_image(wl, beat, w_az, t0=t0)
+    assert rel_l2(img, ref) <= tol
+    check_peaks(img, ref, peak_windows(wl))
+    rng = np.random.Generator(np.random.PCG64(8))
+    fd = rng.uniform(-1.5, 1.5, wl.grid.nx * wl.grid.ny).astype(np.float32)
+    img_fd = gpu_image(plan, wl, beat, w_az, fdopp=fd)
+    assert rel_l2(img_fd, oracle_image(wl, beat, w_az, t0=t0, fd_idx=fd.astype(np.float64))) <= tol
+    first = oracle_image(wl, beat, w_az)
+    assert rel_l2(img, first) > 5 * tol
+
+
 def test_doppler_offsets_refocus_a_moving_platform(torch):
     """Alg. 2's per-pixel f_doppler(p) on a scene recorded with the antennas
     moving during each chirp (20 m/s, targets ahead of the track, offsets of
