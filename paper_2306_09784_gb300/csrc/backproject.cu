@@ -410,6 +410,46 @@ __device__ __forceinline__ void accumulate(float idx, uint32_t ac, float kap, fl
     acc_im = fmaf(vim, cs, acc_im);
 }
 
+// Blackwell's packed FP32 pairs: one instruction issues two FP32 operations,
+// each rounded as its scalar form.  Pixels 2h and 2h + 1 of a thread share
+// each pair, which cuts the pixel loop's instruction count by a fifth (the
+// loop is issue-bound; the FMA pipe does the same work).
+__device__ __forceinline__ float2 ffma2(float2 x, float2 y, float2 z) { return __ffma2_rn(x, y, z); }
+__device__ __forceinline__ float2 fmul2(float2 x, float2 y) { return __fmul2_rn(x, y); }
+__device__ __forceinline__ float2 bcast(float v) { return make_float2(v, v); }
+
+// accumulate() for the pixel pair (2h, 2h + 1) of one pulse and Rx.  The
+// imaginary part is kept as two sums, sum vre sn in acc_im and
+// sum (-vim) cs in acc_imb (subtracted by the caller), so that every packed
+// product has operands of the sign they are computed with; -vim itself comes
+// from one scalar FMA with negated operands.
+__device__ __forceinline__ void accumulate2(float2 idx, uint32_t ac, float2 kap, float2 nkap, float2 kapm,
+                                            float (&acc_re)[kPxPerThread], float (&acc_im)[kPxPerThread],
+                                            float (&acc_imb)[kPxPerThread], int h) {
+    const float2 tm = __fadd2_rd(idx, bcast(kMagic));
+    const float2 g = ffma2(idx, kap, ffma2(nkap, tm, kapm));
+    const float4 e0 = lds128((__float_as_uint(tm.x) << 4) + ac);
+    const float4 e1 = lds128((__float_as_uint(tm.y) << 4) + ac);
+    const float2 vre = make_float2(fmaf(g.x, e0.z, e0.x), fmaf(g.y, e1.z, e1.x));
+    const float2 vimn = make_float2(fmaf(-g.x, e0.w, -e0.y), fmaf(-g.y, e1.w, -e1.y));
+    float2 sn, cs;
+    sincos_approx(g.x, sn.x, cs.x);
+    sincos_approx(g.y, sn.y, cs.y);
+    float2 re = make_float2(acc_re[2 * h], acc_re[2 * h + 1]);
+    float2 im = make_float2(acc_im[2 * h], acc_im[2 * h + 1]);
+    float2 imb = make_float2(acc_imb[2 * h], acc_imb[2 * h + 1]);
+    re = ffma2(vre, cs, re);
+    im = ffma2(vre, sn, im);
+    re = ffma2(vimn, sn, re);
+    imb = ffma2(vimn, cs, imb);
+    acc_re[2 * h] = re.x;
+    acc_re[2 * h + 1] = re.y;
+    acc_im[2 * h] = im.x;
+    acc_im[2 * h + 1] = im.y;
+    acc_imb[2 * h] = imb.x;
+    acc_imb[2 * h + 1] = imb.y;
+}
+
 // PU consecutive pulses of the expansion loop, unrolled together so that
 // RG x PU x 4 updates per thread are independent (latency hiding for small
 // Rx counts).
@@ -422,23 +462,29 @@ __device__ __forceinline__ void expand_pulses(const BpArgs &a, const float4 *txr
                                               const float (&fdi)[kPxPerThread],
                                               float (&acc_re)[kPxPerThread],
                                               float (&acc_im)[kPxPerThread]) {
+    constexpr int H = kPxPerThread / 2;
     const int R = a.R;
     const float two_a1 = 2.0f * a.a1f;
-    const float kap = a.kappa, kapm = a.kappa_magic;
-    float u[PU][kPxPerThread], ay[PU][kPxPerThread], kk[PU][kPxPerThread];
+    const float2 kap = bcast(a.kappa), nkap = bcast(-a.kappa), kapm = bcast(a.kappa_magic);
+    float2 u[PU][H], ay[PU][H], nkk[PU][H];
+    float acc_imb[kPxPerThread];
+#pragma unroll
+    for (int j = 0; j < kPxPerThread; ++j) acc_imb[j] = 0.f;
 #pragma unroll
     for (int q = 0; q < PU; ++q) {
         const float4 t4 = txr[p + q];
         const float cidx = __int_as_float(txc[p + q].x);
 #pragma unroll
-        for (int j = 0; j < kPxPerThread; ++j) {
-            float y;
-            const float dt = range_delta(t4, dx[j], dy[j], hd2[j], y);
+        for (int h = 0; h < H; ++h) {
+            float2 y;
+            const float2 dt = make_float2(range_delta(t4, dx[2 * h], dy[2 * h], hd2[2 * h], y.x),
+                                          range_delta(t4, dx[2 * h + 1], dy[2 * h + 1], hd2[2 * h + 1], y.y));
             // index of the Tx part (twice the Tx range) and, with w = a / 2,
             // a1 (d_rx - d_tx) = w (2 a1 / d - w 2 a1 / d^3)
-            u[q][j] = fmaf(two_a1, dt, FD ? cidx + fdi[j] : cidx);
-            ay[q][j] = two_a1 * y;
-            kk[q][j] = ay[q][j] * (y * y);
+            const float2 c2 = FD ? make_float2(cidx + fdi[2 * h], cidx + fdi[2 * h + 1]) : bcast(cidx);
+            u[q][h] = ffma2(bcast(two_a1), dt, c2);
+            ay[q][h] = fmul2(bcast(two_a1), y);
+            nkk[q][h] = fmul2(fmul2(bcast(-two_a1), y), fmul2(y, y));
         }
     }
     for (int r0 = 0; r0 < R; r0 += RG) {
@@ -449,16 +495,22 @@ __device__ __forceinline__ void expand_pulses(const BpArgs &a, const float4 *txr
                 const float4 o4 = rxt[(p + q) * R + r0 + rr];
                 const uint32_t ac = __float_as_uint(o4.w);
 #pragma unroll
-                for (int j = 0; j < kPxPerThread; ++j) {
+                for (int h = 0; h < H; ++h) {
                     // w = a / 2 = (|o|^2/2 - (p - q_tx).o) / 2 (rxt holds halved constants)
-                    const float w = AXIS ? fmaf(o4.x, dx[j], o4.z) : fmaf(o4.x, dx[j], fmaf(o4.y, dy[j], o4.z));
-                    const float m1 = fmaf(-w, kk[q][j], ay[q][j]);
-                    const float idx = fmaf(w, m1, u[q][j]);
-                    accumulate(idx, ac, kap, kapm, acc_re[j], acc_im[j]);
+                    const float2 dx2 = make_float2(dx[2 * h], dx[2 * h + 1]);
+                    const float2 w = AXIS ? ffma2(bcast(o4.x), dx2, bcast(o4.z))
+                                          : ffma2(bcast(o4.x), dx2,
+                                                  ffma2(bcast(o4.y), make_float2(dy[2 * h], dy[2 * h + 1]),
+                                                        bcast(o4.z)));
+                    const float2 m1 = ffma2(w, nkk[q][h], ay[q][h]);
+                    const float2 idx = ffma2(w, m1, u[q][h]);
+                    accumulate2(idx, ac, kap, nkap, kapm, acc_re, acc_im, acc_imb, h);
                 }
             }
         }
     }
+#pragma unroll
+    for (int j = 0; j < kPxPerThread; ++j) acc_im[j] -= acc_imb[j];  // once per PU pulses
 }
 
 // Expansion loop over one pulse block (far field, small Rx offsets).  When
