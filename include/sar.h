@@ -291,8 +291,10 @@ int sar_batch_get_info(const sar_batch *batch, int32_t *n_jobs, int64_t *units, 
  * range-compressed, then backprojected in rounds: every round is ONE
  * persistent batched launch over the next chunk_pulses chirps of every
  * active request, accumulated into the request's device-resident image.
- * Requests that arrive while a round runs join the next round; finished ones
- * leave.  Admission is bounded by max_inflight and by an HBM budget (one
+ * Requests that arrive while a round runs join the first round launched after
+ * their upload and range compression have completed; finished ones leave.
+ * Larger chunk_pulses means fewer rounds (less per-round cost; 1024 is a good
+ * value for frames of a few thousand chirps).  Admission is bounded by max_inflight and by an HBM budget (one
  * device pool allocated at creation and sub-allocated per request); a request
  * waits in arrival order until its buffers fit.  A request's image equals its
  * stand-alone sar_range_compress + sar_backproject result up to FP32

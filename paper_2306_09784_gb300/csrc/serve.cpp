@@ -212,8 +212,19 @@ int start_request(sar_server *s, Request *q) {
 int launch_round(sar_server *s, std::vector<Request *> &work, bool *launched) {
     *launched = false;
     std::vector<Request *> part;
-    for (Request *q : work)
-        if (q->state == SAR_REQ_RUNNING && !q->cancel && q->next_pulse < q->r.M) part.push_back(q);
+    for (Request *q : work) {
+        if (q->state != SAR_REQ_RUNNING || q->cancel || q->next_pulse >= q->r.M) continue;
+        if (!q->joined) {
+            // a request joins once its upload and range compression are done,
+            // so that a round never waits on copies still in flight (requests
+            // admitted together would otherwise hold the first round until
+            // the last upload finished)
+            const cudaError_t e = cudaEventQuery(q->rc_ev);
+            if (e == cudaErrorNotReady) continue;
+            if (e != cudaSuccess) return SAR_ECUDA;
+        }
+        part.push_back(q);
+    }
     if (part.empty()) return SAR_OK;
     const int k = s->parity;
     if (s->round_pending[k]) {  // at most two rounds in flight
