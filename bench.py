@@ -379,7 +379,7 @@ def bench_served(dev, duration_s=3.0, seed=7, n_saturate=40):
                            w=torch.from_numpy(synth.azimuth_weights(2048).astype(np.float32)).pin_memory(),
                            qt=torch.from_numpy(q_tx).pin_memory(),
                            qr=torch.from_numpy(np.ascontiguousarray(q_rx)).pin_memory()))
-    srv = sar.Server(hbm_budget=8 << 30, max_inflight=64, queue_capacity=4096, chunk_pulses=1024)
+    srv = sar.Server(hbm_budget=8 << 30, max_inflight=64, queue_capacity=4096, chunk_pulses=2048)
 
     def submit(rd, M, out):
         return srv.submit(rd["plan"], rd["beat"], rd["qt"], rd["qr"], w_az=rd["w"], image=out, M=M)

@@ -293,8 +293,9 @@ int sar_batch_get_info(const sar_batch *batch, int32_t *n_jobs, int64_t *units, 
  * active request, accumulated into the request's device-resident image.
  * Requests that arrive while a round runs join the first round launched after
  * their upload and range compression have completed; finished ones leave.
- * Larger chunk_pulses means fewer rounds (less per-round cost; 1024 is a good
- * value for frames of a few thousand chirps).  Admission is bounded by max_inflight and by an HBM budget (one
+ * Larger chunk_pulses means fewer rounds (less per-round cost); a value at
+ * least the frames' chirp count (one round per frame) gave the best
+ * throughput and no worse latency on frames of 256-2048 chirps.  Admission is bounded by max_inflight and by an HBM budget (one
  * device pool allocated at creation and sub-allocated per request); a request
  * waits in arrival order until its buffers fit.  A request's image equals its
  * stand-alone sar_range_compress + sar_backproject result up to FP32

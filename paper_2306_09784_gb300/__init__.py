@@ -380,7 +380,7 @@ class Server:
     referenced until the request is released."""
 
     def __init__(self, hbm_budget: int, max_inflight: int = 64, queue_capacity: int = 1024,
-                 chunk_pulses: int = 1024):
+                 chunk_pulses: int = 2048):
         self._lib = load_library()
         self._s = None
         cfg = ServerConfig(hbm_budget_bytes=hbm_budget, max_inflight=max_inflight,

@@ -369,8 +369,11 @@ void worker_main(sar_server *s) {
             }
             if (any) s->done_cv.notify_all();
             if (!launched && admitted.empty()) {
-                // nothing new to launch: wait for a submission or GPU progress
-                s->cv.wait_for(lk, std::chrono::microseconds(100));
+                // nothing new to launch: wait for a submission or GPU progress.
+                // While requests are in flight, poll at a short interval so
+                // that a range compression finishing (a request ready to join)
+                // or a round completing is acted on within ~20 us.
+                s->cv.wait_for(lk, std::chrono::microseconds(s->active.empty() ? 100 : 20));
             }
         }
     }
