@@ -372,6 +372,20 @@ def test_time_origin_chirp_centre(torch, small, precision):
     assert rel_l2(img, first) > 5 * tol
 
 
+def test_time_origin_chirp_centre_conjugate(torch, small):
+    """Chirp-centre time origin under the conjugate convention: the image is
+    the conjugate of the +1 convention's centred image, and equals the
+    oracle's centred transform with sign -1."""
+    import paper_2306_09784_gb300 as sar
+    wl, beat, w_az = small
+    t0 = (wl.radar.n_samples - 1) / 2.0
+    plan = make_plan(wl, phase_sign=-1, time_origin=sar.ORIGIN_CHIRP_CENTRE)
+    bc = np.conj(beat).astype(np.complex64)
+    img = gpu_image(plan, wl, bc, w_az)
+    assert rel_l2(img, oracle_image(wl, bc, w_az, sign=-1, t0=t0)) <= TOL_FP32
+    assert rel_l2(img, np.conj(oracle_image(wl, beat, w_az, t0=t0))) <= TOL_FP32
+
+
 def test_doppler_offsets_refocus_a_moving_platform(torch):
     """Alg. 2's per-pixel f_doppler(p) on a scene recorded with the antennas
     moving during each chirp (20 m/s, targets ahead of the track, offsets of
