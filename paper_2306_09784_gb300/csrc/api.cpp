@@ -55,7 +55,7 @@ struct sar_plan {
     void *s_prof = nullptr, *s_img = nullptr;
     // its copy stream and events (created on first use)
     cudaStream_t s_copy = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_chunk[2] = {nullptr, nullptr};
+    cudaEvent_t ev_start = nullptr, ev_chunk[2] = {nullptr, nullptr}, ev_traj = nullptr;
     size_t budget = 0, used = 0;
     std::vector<void *> allocs;
 };
@@ -145,7 +145,7 @@ void free_plan(sar_plan *pl) {
     cudaDeviceSynchronize();
     for (void *p : pl->allocs) cudaFree(p);
     if (pl->s_copy) cudaStreamDestroy(pl->s_copy);
-    for (cudaEvent_t e : {pl->ev_start, pl->ev_chunk[0], pl->ev_chunk[1]})
+    for (cudaEvent_t e : {pl->ev_start, pl->ev_chunk[0], pl->ev_chunk[1], pl->ev_traj})
         if (e) cudaEventDestroy(e);
     delete pl;
 }
@@ -826,24 +826,29 @@ int sar_form_image_host(sar_plan *pl, const void *beat_host, int32_t M, const fl
             pl->s_copy = nullptr;
             return SAR_ECUDA;
         }
-        for (cudaEvent_t *e : {&pl->ev_start, &pl->ev_chunk[0], &pl->ev_chunk[1]})
+        for (cudaEvent_t *e : {&pl->ev_start, &pl->ev_chunk[0], &pl->ev_chunk[1], &pl->ev_traj})
             if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return SAR_ECUDA;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    // Two-chunk pipeline: the copy stream uploads the trajectory, w_sar and
-    // the first ~1/8 of the chirps (whole pulse blocks), then the rest; the
-    // caller's stream range-compresses and backprojects the first chunk while
-    // the rest is still in flight, then the rest (accumulating into the image).
-    int cut = (M / 8) / pl->Mb * pl->Mb;
-    if (cut < pl->Mb || cut >= M) cut = M;
+    // Two-chunk pipeline.  The copy stream uploads w_sar and the first chunk
+    // of chirps (whole pulse blocks), then the trajectory, then the rest; the
+    // caller's stream range-compresses the first chunk while the trajectory
+    // is in flight, backprojects it while the rest is, then the rest
+    // (accumulating into the image).  The first chunk is the smallest whose
+    // backprojection should outlast the upload of the rest, from a model of
+    // the kernel's update rate (~1.3e12 updates/s) and of pinned host-to-device
+    // bandwidth (~200 GB/s): only its upload is exposed.  Frames whose whole
+    // upload takes less than ~40 us are not split (a second range compression
+    // and backprojection launch would cost about as much).
+    const size_t row_bytes = (size_t)R * N * 8;
+    const double t_bp = (double)pl->n_pixels * R / 1.3e12, t_up = (double)row_bytes / 2.0e11;
+    int cut = (int)std::ceil(M * t_up / (t_bp + t_up) / pl->Mb) * pl->Mb;
+    cut = std::max(cut, pl->Mb);
+    if (cut >= M || M * t_up < 4.0e-5) cut = M;
     const int bounds[3] = {0, cut, M};
     const int n_chunks = cut < M ? 2 : 1;
-    const size_t row_bytes = (size_t)R * N * 8;
     bool ok = cudaEventRecord(pl->ev_start, s) == cudaSuccess &&
               cudaStreamWaitEvent(pl->s_copy, pl->ev_start, 0) == cudaSuccess;
-    ok = ok && cudaMemcpyAsync(pl->s_qtx, q_tx_host, (size_t)M * 16, cudaMemcpyHostToDevice, pl->s_copy) == cudaSuccess;
-    ok = ok &&
-         cudaMemcpyAsync(pl->s_qrx, q_rx_host, (size_t)M * R * 16, cudaMemcpyHostToDevice, pl->s_copy) == cudaSuccess;
     if (w_az_host)
         ok = ok &&
              cudaMemcpyAsync(pl->s_waz, w_az_host, (size_t)M * 4, cudaMemcpyHostToDevice, pl->s_copy) == cudaSuccess;
@@ -852,6 +857,14 @@ int sar_form_image_host(sar_plan *pl, const void *beat_host, int32_t M, const fl
         ok = cudaMemcpyAsync((unsigned char *)pl->s_beat + off, (const unsigned char *)beat_host + off, bytes,
                              cudaMemcpyHostToDevice, pl->s_copy) == cudaSuccess &&
              cudaEventRecord(pl->ev_chunk[c], pl->s_copy) == cudaSuccess;
+        if (c == 0) {
+            ok = ok &&
+                 cudaMemcpyAsync(pl->s_qtx, q_tx_host, (size_t)M * 16, cudaMemcpyHostToDevice, pl->s_copy) ==
+                     cudaSuccess &&
+                 cudaMemcpyAsync(pl->s_qrx, q_rx_host, (size_t)M * R * 16, cudaMemcpyHostToDevice, pl->s_copy) ==
+                     cudaSuccess &&
+                 cudaEventRecord(pl->ev_traj, pl->s_copy) == cudaSuccess;
+        }
     }
     if (!ok) return SAR_ECUDA;
     const int mode = pl->fp16 ? kRcProfileF16 : kRcProfileF32;
@@ -861,6 +874,7 @@ int sar_form_image_host(sar_plan *pl, const void *beat_host, int32_t M, const fl
         rc = rc_launch_part(pl, (const unsigned char *)pl->s_beat + (size_t)m0 * row_bytes, m0, Mc, M,
                             w_az_host ? pl->s_waz + m0 : nullptr, pl->s_prof, mode, s);
         if (rc) return rc;
+        if (c == 0 && cudaStreamWaitEvent(s, pl->ev_traj, 0) != cudaSuccess) return SAR_ECUDA;
         rc = bp_launch(pl, pl->s_prof, Mc, pl->s_qtx + 2 * (size_t)m0, pl->s_qrx + 2 * (size_t)m0 * R, nullptr,
                        pl->s_img, c > 0, s, m0, M);
         if (rc) return rc;

@@ -459,6 +459,30 @@ def test_host_entry_point(torch, small):
     assert np.array_equal(out.numpy(), dev)
 
 
+def test_host_entry_point_two_chunks(torch):
+    """A frame large enough for sar_form_image_host to upload in two chunks
+    (512^2 px, 1024 chirps x 4 Rx x 512 samples, FP16): the image equals the
+    device path up to FP32 summation order (the second chunk accumulates onto
+    the first) and the oracle within tolerance at sampled pixels."""
+    import torch as t
+    wl = synth.make_workload("full")
+    beat = synth.workload_beat(wl, device="cuda")
+    w_az = np.hanning(wl.n_pulses)
+    plan = make_plan(wl, precision=1)
+    dev = gpu_image(plan, wl, beat, w_az)
+    hb = t.from_numpy(beat).pin_memory()
+    hw = t.from_numpy(w_az.astype(np.float32)).pin_memory()
+    hq = t.from_numpy(wl.q_tx).pin_memory()
+    hr = t.from_numpy(np.ascontiguousarray(wl.q_rx)).pin_memory()
+    out = t.empty(plan.n_pixels, dtype=t.complex64).pin_memory()
+    plan.form_image_host(hb, hq, hr, out, w_az=hw)
+    img = out.numpy()
+    assert rel_l2(img, dev) < 1e-5
+    idx = sample_pixels(len(img), 512)
+    ref = oracle_image(wl, beat, w_az, px=wl.grid.pixels()[idx])
+    assert rel_l2(img[idx], ref) <= TOL_FP16
+
+
 def test_invalid_arguments(torch, small):
     import paper_2306_09784_gb300 as sar
     wl, beat, w_az = small
