@@ -47,6 +47,10 @@
 namespace sar {
 namespace {
 
+// Fix-up kernels: threads per CTA and pixels per thread of one tile.
+constexpr int kFixupThreads = 256;
+constexpr int kFixupPx = kTilePx / kFixupThreads;
+
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: adding it (rounding down) floors to an integer
 constexpr uint32_t kMagicBits = 0x4B400000u;
 // Truncation bound of the expansion loop, in bins of the index.
@@ -762,7 +766,7 @@ __global__ void __launch_bounds__(kBpThreads, 2) backproject_batch_kernel(BpBatc
 }
 
 // Fix-up of the batched form: one CTA per tile of every request.
-__global__ void __launch_bounds__(256) bp_batch_fixup_kernel(BpBatchArgs B) {
+__global__ void __launch_bounds__(kFixupThreads) bp_batch_fixup_kernel(BpBatchArgs B) {
     const int gt = blockIdx.x;
     int lo = 0, hi = B.n_jobs - 1;
     while (lo < hi) {
@@ -777,28 +781,35 @@ __global__ void __launch_bounds__(256) bp_batch_fixup_kernel(BpBatchArgs B) {
     const int ia = (int)(((tb + 1) * B.G - 1) / B.units);
     const int ib = (int)((te * B.G - 1) / B.units);
     if (ia == ib) return;
-    for (int s = threadIdx.x; s < kTilePx; s += blockDim.x) {
-        const int o = a.out_idx[(long long)tile * kTilePx + s];
-        if (o < 0) continue;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int i = ia; i <= ib; ++i) {
-            const long long ui0 = (long long)i * B.units / B.G;
-            const long long slot = (long long)i * 2 + (ui0 >= tb ? 0 : 1);
-            const float2 v = B.scratch[slot * kTilePx + s];
-            acc.x += v.x;
-            acc.y += v.y;
+    float2 acc[kFixupPx];
+#pragma unroll
+    for (int k = 0; k < kFixupPx; ++k) acc[k] = make_float2(0.f, 0.f);
+    for (int i = ia; i <= ib; ++i) {  // CTA order; one slot lookup per CTA
+        const long long ui0 = (long long)i * B.units / B.G;
+        const float2 *part = B.scratch + ((long long)i * 2 + (ui0 >= tb ? 0 : 1)) * kTilePx;
+#pragma unroll
+        for (int k = 0; k < kFixupPx; ++k) {
+            const float2 v = part[threadIdx.x + k * kFixupThreads];
+            acc[k].x += v.x;
+            acc[k].y += v.y;
         }
+    }
+#pragma unroll
+    for (int k = 0; k < kFixupPx; ++k) {
+        const int o = a.out_idx[(long long)tile * kTilePx + threadIdx.x + k * kFixupThreads];
+        if (o < 0) continue;
+        float2 v = acc[k];
         if (a.accumulate) {
             const float2 old = a.image[o];
-            acc.x += old.x;
-            acc.y += old.y;
+            v.x += old.x;
+            v.y += old.y;
         }
-        a.image[o] = acc;
+        a.image[o] = v;
     }
 }
 
 // Sums, in CTA order, the partial sums of tiles that were split across CTAs.
-__global__ void __launch_bounds__(256) bp_fixup_kernel(BpArgs a) {
+__global__ void __launch_bounds__(kFixupThreads) bp_fixup_kernel(BpArgs a) {
     const int tile = blockIdx.x;
     const long long PB = a.blocks_per_tile;
     const long long ua = (long long)tile * PB;
@@ -806,23 +817,30 @@ __global__ void __launch_bounds__(256) bp_fixup_kernel(BpArgs a) {
     const int ia = (int)(((ua + 1) * a.G - 1) / a.units);
     const int ib = (int)(((ub + 1) * a.G - 1) / a.units);
     if (ia == ib) return;
-    for (int s = threadIdx.x; s < kTilePx; s += blockDim.x) {
-        const int o = a.out_idx[(long long)tile * kTilePx + s];
-        if (o < 0) continue;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int i = ia; i <= ib; ++i) {
-            const long long ui0 = (long long)i * a.units / a.G;
-            const long long slot = (long long)i * a.seg_max + (tile - (int)(ui0 / PB));
-            const float2 v = a.partial[slot * kTilePx + s];
-            acc.x += v.x;
-            acc.y += v.y;
+    float2 acc[kFixupPx];
+#pragma unroll
+    for (int k = 0; k < kFixupPx; ++k) acc[k] = make_float2(0.f, 0.f);
+    for (int i = ia; i <= ib; ++i) {  // CTA order; one slot lookup per CTA
+        const long long ui0 = (long long)i * a.units / a.G;
+        const float2 *part = a.partial + ((long long)i * a.seg_max + (tile - (int)(ui0 / PB))) * kTilePx;
+#pragma unroll
+        for (int k = 0; k < kFixupPx; ++k) {
+            const float2 v = part[threadIdx.x + k * kFixupThreads];
+            acc[k].x += v.x;
+            acc[k].y += v.y;
         }
+    }
+#pragma unroll
+    for (int k = 0; k < kFixupPx; ++k) {
+        const int o = a.out_idx[(long long)tile * kTilePx + threadIdx.x + k * kFixupThreads];
+        if (o < 0) continue;
+        float2 v = acc[k];
         if (a.accumulate) {
             const float2 old = a.image[o];
-            acc.x += old.x;
-            acc.y += old.y;
+            v.x += old.x;
+            v.y += old.y;
         }
-        a.image[o] = acc;
+        a.image[o] = v;
     }
 }
 
@@ -907,7 +925,7 @@ cudaError_t launch_backproject_batch(const BpBatchArgs &b, int rg, bool fp16, in
     void *params[] = {&args};
     cudaError_t e = cudaLaunchKernel(k, dim3(b.G), dim3(kBpThreads), params, smem, s);
     if (e != cudaSuccess) return e;
-    bp_batch_fixup_kernel<<<total_tiles, 256, 0, s>>>(b);
+    bp_batch_fixup_kernel<<<total_tiles, kFixupThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -919,7 +937,7 @@ cudaError_t launch_backproject(const BpArgs &a, const BpLaunch &l, cudaStream_t 
     void *params[] = {&args};
     cudaError_t e = cudaLaunchKernel(k, dim3(a.G), dim3(kBpThreads), params, l.smem, s);
     if (e != cudaSuccess) return e;
-    bp_fixup_kernel<<<a.n_tiles, 256, 0, s>>>(a);
+    bp_fixup_kernel<<<a.n_tiles, kFixupThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
