@@ -79,6 +79,13 @@ def alu_peak_updates(sm_mhz: float) -> float:
     return min(SMS * FP32_LANES * hz / ALG_FP32_OPS, SMS * MUFU_LANES * hz / ALG_MUFU_OPS)
 
 
+def measured_peak_updates(pipes: dict) -> float:
+    """The same roofline from measured pipe rates (sar_alu_peaks): the best
+    FP32 lane rate (scalar or packed FMA) / 17 and the MUFU rate / 3."""
+    fp32 = max(pipes["fma_lane_ops_per_s"], pipes["ffma2_lane_ops_per_s"])
+    return min(fp32 / ALG_FP32_OPS, pipes["mufu_ops_per_s"] / ALG_MUFU_OPS)
+
+
 def max_over_ranks(seconds: float, ws: int, device=None) -> float:
     """Slowest rank's timed-region length (a timing reduction, not a data-path
     collective)."""
@@ -486,6 +493,9 @@ def run_ours(args):
         shape = plan.set_launch(rg, minb, mb)
     else:
         shape = plan.autotune(prof, M, qt, qr, image, stream=stream)
+    # measured FP32 and MUFU pipe throughput (untimed set-up): a cross-check
+    # of the nominal lane counts the ALU roofline is derived from
+    pipes = sar.alu_peaks()
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
     upd = P * M * R
 
@@ -575,7 +585,10 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": kernel_traffic(),
                      "peak_basis": "min(152 SM x 128 FP32 lanes / 17 ops, 152 SM x 16 MUFU "
                                    "lanes / 3 ops) per update at the 2070 MHz max SM clock",
-                     "frac_at_sampled_clock": upd / bp_avg_s / alu_peak_updates(sm_mhz)},
+                     "frac_at_sampled_clock": upd / bp_avg_s / alu_peak_updates(sm_mhz),
+                     "measured_pipes": pipes,
+                     "peak_measured": measured_peak_updates(pipes) / 1e9,
+                     "frac_of_measured": upd / bp_avg_s / measured_peak_updates(pipes)},
         "roofline_range_compress": rc_roofline(plan, M, R, r.n_samples, statistics.mean(rc_ms)),
         "clocks": clocks,
         "e2e": {"value": upd / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

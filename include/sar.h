@@ -412,6 +412,19 @@ int sar_plan_set_launch(sar_plan *plan, int32_t rx_group, int32_t regs_ctas_per_
  */
 int sar_plan_check_errors(sar_plan *plan);
 
+/*
+ * Measured throughput of the two pipes that bound the backprojection, on the
+ * current device (no counterpart in the paper; used to check the kernel's
+ * ALU roofline against measured rates).  Runs three ~1 ms microbenchmark
+ * kernels, each over 4 CTAs of 256 threads per SM with 8 independent
+ * dependency chains per thread, and reports the best of three timed
+ * launches: FP32 FMA lane-ops/s with scalar FFMA, with packed FFMA2 (2 lane
+ * ops each) and MUFU operations/s (sin.approx).  Synchronous; allocates and
+ * frees a small device buffer.  Errors: SAR_EINVAL (null pointers),
+ * SAR_ENOMEM, SAR_ECUDA.
+ */
+int sar_alu_peaks(double *fma_lane_ops_per_s, double *ffma2_lane_ops_per_s, double *mufu_ops_per_s);
+
 /* Static text for a status code. */
 const char *sar_status_string(int status);
 

@@ -31,6 +31,7 @@ EXPORTS = (
     "sar_batch_commit", "sar_batch_launch", "sar_batch_get_info",
     "sar_server_create", "sar_server_destroy", "sar_submit", "sar_poll", "sar_wait",
     "sar_release", "sar_server_get_stats", "sar_plan_autotune", "sar_plan_set_launch",
+    "sar_alu_peaks",
 )
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 
@@ -136,6 +137,8 @@ def load_library(path: str = LIB_PATH):
     lib.sar_status_string.argtypes = [ctypes.c_int]
     lib.sar_status_string.restype = ctypes.c_char_p
     lib.sar_version.argtypes = []
+    dptr = ctypes.POINTER(ctypes.c_double)
+    lib.sar_alu_peaks.argtypes = [dptr, dptr, dptr]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("sar_plan_destroy", "sar_status_string", "sar_batch_destroy",
@@ -143,6 +146,16 @@ def load_library(path: str = LIB_PATH):
             fn.restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+def alu_peaks() -> dict:
+    """Measured FP32 FMA (scalar and packed) and MUFU throughput of the
+    current CUDA device (sar_alu_peaks), in lane operations per second."""
+    lib = load_library()
+    f, f2, m = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib.sar_alu_peaks(ctypes.byref(f), ctypes.byref(f2), ctypes.byref(m)), "sar_alu_peaks")
+    return {"fma_lane_ops_per_s": f.value, "ffma2_lane_ops_per_s": f2.value,
+            "mufu_ops_per_s": m.value}
 
 
 def status_string(status: int) -> str:
