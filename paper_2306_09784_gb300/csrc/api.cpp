@@ -82,6 +82,10 @@ struct sar_batch {
     int tiles = 0;
     bool committed = false, upload_pending = false;
     BpArgs *h_jobs = nullptr;    // in the order added
+    // One pinned upload blob and its device copy, [ub | tb | sorted jobs], so
+    // that a commit is a single host-to-device copy:
+    unsigned char *h_blob = nullptr, *d_blob = nullptr;
+    size_t jobs_off = 0;
     BpArgs *h_sorted = nullptr;  // grouped by class (upload source)
     long long *h_ub = nullptr;   // per-class prefix sums of units
     int *h_tb = nullptr;         // per-class prefix sums of tiles
@@ -89,6 +93,9 @@ struct sar_batch {
     long long *d_ub = nullptr;
     int *d_tb = nullptr;
     float2 *d_scratch = nullptr;
+    // occupancy of each class's kernel for the shared-memory size last seen
+    size_t occ_smem[kBatchClasses] = {};
+    int occ_ctas[kBatchClasses] = {};
     cudaEvent_t uploaded = nullptr;
     int n_classes = 0;
     BatchClass cls[kBatchClasses];
@@ -902,15 +909,22 @@ int sar_batch_create(int32_t max_jobs, sar_batch **out) {
     b->num_sms = prop.multiProcessorCount;
     b->g_cap = b->num_sms * 2;  // the batch kernel runs at most two CTAs per SM
     const size_t n_pref = (size_t)max_jobs + kBatchClasses;
+    const size_t tb_off = sizeof(long long) * n_pref;
+    b->jobs_off = (tb_off + sizeof(int) * n_pref + 15) & ~size_t(15);
+    const size_t blob = b->jobs_off + sizeof(BpArgs) * max_jobs;
     bool ok = cudaMallocHost((void **)&b->h_jobs, sizeof(BpArgs) * max_jobs) == cudaSuccess &&
-              cudaMallocHost((void **)&b->h_sorted, sizeof(BpArgs) * max_jobs) == cudaSuccess &&
-              cudaMallocHost((void **)&b->h_ub, sizeof(long long) * n_pref) == cudaSuccess &&
-              cudaMallocHost((void **)&b->h_tb, sizeof(int) * n_pref) == cudaSuccess &&
-              cudaMalloc((void **)&b->d_jobs, sizeof(BpArgs) * max_jobs) == cudaSuccess &&
-              cudaMalloc((void **)&b->d_ub, sizeof(long long) * n_pref) == cudaSuccess &&
-              cudaMalloc((void **)&b->d_tb, sizeof(int) * n_pref) == cudaSuccess &&
+              cudaMallocHost((void **)&b->h_blob, blob) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_blob, blob) == cudaSuccess &&
               cudaMalloc((void **)&b->d_scratch, sizeof(float2) * kTilePx * 2 * (size_t)b->g_cap) == cudaSuccess &&
               cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) {
+        b->h_ub = reinterpret_cast<long long *>(b->h_blob);
+        b->h_tb = reinterpret_cast<int *>(b->h_blob + tb_off);
+        b->h_sorted = reinterpret_cast<BpArgs *>(b->h_blob + b->jobs_off);
+        b->d_ub = reinterpret_cast<long long *>(b->d_blob);
+        b->d_tb = reinterpret_cast<int *>(b->d_blob + tb_off);
+        b->d_jobs = reinterpret_cast<BpArgs *>(b->d_blob + b->jobs_off);
+    }
     if (!ok) {
         cudaGetLastError();
         sar_batch_destroy(b);
@@ -924,12 +938,8 @@ void sar_batch_destroy(sar_batch *b) {
     if (!b) return;
     cudaDeviceSynchronize();
     if (b->h_jobs) cudaFreeHost(b->h_jobs);
-    if (b->h_sorted) cudaFreeHost(b->h_sorted);
-    if (b->h_ub) cudaFreeHost(b->h_ub);
-    if (b->h_tb) cudaFreeHost(b->h_tb);
-    if (b->d_jobs) cudaFree(b->d_jobs);
-    if (b->d_ub) cudaFree(b->d_ub);
-    if (b->d_tb) cudaFree(b->d_tb);
+    if (b->h_blob) cudaFreeHost(b->h_blob);
+    if (b->d_blob) cudaFree(b->d_blob);
     if (b->d_scratch) cudaFree(b->d_scratch);
     if (b->uploaded) cudaEventDestroy(b->uploaded);
     delete b;
@@ -1011,21 +1021,22 @@ int sar_batch_commit(sar_batch *b, void *stream) {
         }
         b->h_ub[c.off + c.n] = c.units;
         b->h_tb[c.off + c.n] = c.tiles;
-        int occ = 0;
-        if (bp_batch_prepare(c.rg, c.fp16, c.smem, &occ) != cudaSuccess || occ < 1) {
-            cudaGetLastError();
-            return SAR_ECUDA;
+        const int k = (c.fp16 ? 4 : 0) + c.rg - 1;
+        int occ = b->occ_smem[k] == c.smem ? b->occ_ctas[k] : 0;
+        if (occ < 1) {
+            if (bp_batch_prepare(c.rg, c.fp16, c.smem, &occ) != cudaSuccess || occ < 1) {
+                cudaGetLastError();
+                return SAR_ECUDA;
+            }
+            b->occ_smem[k] = c.smem;
+            b->occ_ctas[k] = occ;
         }
         c.G = (int)std::min<long long>(std::min(b->g_cap, b->num_sms * occ), c.units);
         b->G = std::max(b->G, c.G);
     }
-    const int n_pref = b->n_jobs + b->n_classes;
     cudaStream_t s = (cudaStream_t)stream;
-    bool ok = cudaMemcpyAsync(b->d_jobs, b->h_sorted, sizeof(BpArgs) * b->n_jobs, cudaMemcpyHostToDevice, s) ==
-                  cudaSuccess &&
-              cudaMemcpyAsync(b->d_ub, b->h_ub, sizeof(long long) * n_pref, cudaMemcpyHostToDevice, s) ==
-                  cudaSuccess &&
-              cudaMemcpyAsync(b->d_tb, b->h_tb, sizeof(int) * n_pref, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+    bool ok = cudaMemcpyAsync(b->d_blob, b->h_blob, b->jobs_off + sizeof(BpArgs) * b->n_jobs,
+                              cudaMemcpyHostToDevice, s) == cudaSuccess &&
               cudaEventRecord(b->uploaded, s) == cudaSuccess;
     if (!ok) return SAR_ECUDA;
     b->upload_pending = true;
