@@ -987,6 +987,10 @@ int sar_batch_commit(sar_batch *b, void *stream) {
     }
     DeviceGuard dg(b->device);
     if (!dg.ok) return SAR_ECUDA;
+    if (b->upload_pending) {  // the upload blob is about to be rewritten
+        if (cudaEventSynchronize(b->uploaded) != cudaSuccess) return SAR_ECUDA;
+        b->upload_pending = false;
+    }
     // group the jobs by class, keeping their order within a class
     int count[kBatchClasses] = {0};
     auto key = [](const BpArgs &a) { return (a.fp16 ? 4 : 0) + a.rg - 1; };
