@@ -363,7 +363,9 @@ int sar_server_get_stats(sar_server *server, sar_server_stats *stats);
  * call synchronises `stream`).  The uploads run on a copy stream of the plan
  * in two chunks of chirps, ordered after the work already queued on
  * `stream`; the kernels run on `stream`, the first chunk's while the second
- * chunk is still being copied.  Frames whose upload is short are not split;
+ * chunk is still being copied.  A page-locked, mapped image_host (cudaHostAlloc
+ * memory under unified addressing) is written by the last kernels directly;
+ * any other image_host gets a device-to-host copy.  Frames whose upload is short are not split;
  * a split frame's image equals sar_backproject's up to FP32 summation order
  * (the second chunk accumulates onto the first).  Staging buffers are allocated on first use
  * for max_pulses chirps (counted in the HBM budget).  Calls on one plan must

@@ -674,8 +674,10 @@ bool set_launch(const sar_plan *pl, BpArgs &a, float2 *partial, size_t slots) {
 }
 
 int bp_launch(sar_plan *pl, const void *prof, int M, const double *q_tx, const double *q_rx, const float *fd,
-              void *image, int accumulate, cudaStream_t s, int m0 = 0, int M_tot = 0) {
+              void *image, int accumulate, cudaStream_t s, int m0 = 0, int M_tot = 0,
+              void *image_out = nullptr) {
     BpArgs a = common_bp_args(pl, prof, M, q_tx, q_rx, fd, image, accumulate, m0, M_tot);
+    a.image_out = (float2 *)image_out;
     if (!set_launch(pl, a, pl->d_partial, pl->partial_slots)) return SAR_EINVAL;  // cannot happen
     BpLaunch l{pl->rg, pl->fp16, pl->bp_smem, pl->minb};
     DeviceGuard dg(pl->device);
@@ -874,6 +876,16 @@ int sar_form_image_host(sar_plan *pl, const void *beat_host, int32_t M, const fl
         }
     }
     if (!ok) return SAR_ECUDA;
+    // A page-locked, mapped image_host (e.g. cudaHostAlloc memory under
+    // unified addressing) is written by the last chunk's kernels directly,
+    // tile by tile while they run, instead of by one copy after them.
+    void *img_dev = nullptr;
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, image_host) == cudaSuccess) {
+        if (pa.type == cudaMemoryTypeHost && pa.devicePointer && aligned(pa.devicePointer, 8)) img_dev = pa.devicePointer;
+    } else {
+        cudaGetLastError();
+    }
     const int mode = pl->fp16 ? kRcProfileF16 : kRcProfileF32;
     for (int c = 0; c < n_chunks; ++c) {
         const int m0 = bounds[c], Mc = bounds[c + 1] - bounds[c];
@@ -883,10 +895,11 @@ int sar_form_image_host(sar_plan *pl, const void *beat_host, int32_t M, const fl
         if (rc) return rc;
         if (c == 0 && cudaStreamWaitEvent(s, pl->ev_traj, 0) != cudaSuccess) return SAR_ECUDA;
         rc = bp_launch(pl, pl->s_prof, Mc, pl->s_qtx + 2 * (size_t)m0, pl->s_qrx + 2 * (size_t)m0 * R, nullptr,
-                       pl->s_img, c > 0, s, m0, M);
+                       pl->s_img, c > 0, s, m0, M, c == n_chunks - 1 ? img_dev : nullptr);
         if (rc) return rc;
     }
-    if (cudaMemcpyAsync(image_host, pl->s_img, (size_t)pl->n_pixels * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (!img_dev &&
+        cudaMemcpyAsync(image_host, pl->s_img, (size_t)pl->n_pixels * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return SAR_ECUDA;
     return cudaStreamSynchronize(s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
 }

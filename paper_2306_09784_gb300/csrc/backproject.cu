@@ -680,6 +680,7 @@ __device__ __forceinline__ void process_segment(const BpArgs &a, const Smem &sm,
     }
 
     if (partial_dst == nullptr) {
+        float2 *dst = a.image_out ? a.image_out : a.image;
 #pragma unroll
         for (int j = 0; j < kPxPerThread; ++j) {
             if (oi[j] < 0) continue;
@@ -689,7 +690,7 @@ __device__ __forceinline__ void process_segment(const BpArgs &a, const Smem &sm,
                 v.x += o.x;
                 v.y += o.y;
             }
-            a.image[oi[j]] = v;
+            dst[oi[j]] = v;
         }
     } else {
 #pragma unroll
@@ -830,6 +831,7 @@ __global__ void __launch_bounds__(kFixupThreads) bp_fixup_kernel(BpArgs a) {
             acc[k].y += v.y;
         }
     }
+    float2 *dst = a.image_out ? a.image_out : a.image;
 #pragma unroll
     for (int k = 0; k < kFixupPx; ++k) {
         const int o = a.out_idx[(long long)tile * kTilePx + threadIdx.x + k * kFixupThreads];
@@ -840,7 +842,7 @@ __global__ void __launch_bounds__(kFixupThreads) bp_fixup_kernel(BpArgs a) {
             v.x += old.x;
             v.y += old.y;
         }
-        a.image[o] = v;
+        dst[o] = v;
     }
 }
 

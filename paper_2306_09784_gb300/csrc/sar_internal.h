@@ -60,6 +60,7 @@ struct BpArgs {
     const double *q_rx;        // [M][R][2]
     const float *fdopp;        // [n_pixels] or null
     float2 *image;             // [n_pixels]
+    float2 *image_out;         // where the result is written (null: image); may be mapped host memory
     float2 *partial;           // [G * seg_max][kTilePx]
     int *err;                  // device error flags
     const float2 *pix;         // [n_tiles][kTilePx] (dx, dy) from the tile reference

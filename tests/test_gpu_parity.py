@@ -457,6 +457,10 @@ def test_host_entry_point(torch, small):
     out = t.empty(plan.n_pixels, dtype=t.complex64).pin_memory()
     plan.form_image_host(hb, hq, hr, out, w_az=hw)
     assert np.array_equal(out.numpy(), dev)
+    # a pageable destination takes the copy path instead of the kernels' own writes
+    out_pageable = t.empty(plan.n_pixels, dtype=t.complex64)
+    plan.form_image_host(hb, hq, hr, out_pageable, w_az=hw)
+    assert np.array_equal(out_pageable.numpy(), dev)
 
 
 def test_host_entry_point_two_chunks(torch):
@@ -478,6 +482,9 @@ def test_host_entry_point_two_chunks(torch):
     plan.form_image_host(hb, hq, hr, out, w_az=hw)
     img = out.numpy()
     assert rel_l2(img, dev) < 1e-5
+    out_pageable = t.empty(plan.n_pixels, dtype=t.complex64)
+    plan.form_image_host(hb, hq, hr, out_pageable, w_az=hw)
+    assert np.array_equal(out_pageable.numpy(), img)
     idx = sample_pixels(len(img), 512)
     ref = oracle_image(wl, beat, w_az, px=wl.grid.pixels()[idx])
     assert rel_l2(img[idx], ref) <= TOL_FP16
