@@ -151,7 +151,11 @@ typedef struct sar_plan_info {
  * builds the FP64 tables (range window, transform twiddles, per-bin phase
  * rotation, pixel tiles) and allocates the plan's device memory.
  * hbm_budget_bytes bounds that memory (0 = no bound): SAR_ENOMEM if it
- * would be exceeded.  *out receives the plan (NULL on error).
+ * would be exceeded.  *out receives the plan (NULL on error).  SAR_EINVAL,
+ * before any CUDA call, for invalid parameters, a null or empty grid (nx or
+ * ny < 1, n_pixels < 1 for a point list), more than 2^30 points or a
+ * non-finite Cartesian origin or spacing; non-finite listed points give
+ * SAR_EINVAL too.
  */
 int sar_plan_create(const sar_radar_params *params, const sar_grid *grid,
                     size_t hbm_budget_bytes, sar_plan **out);

@@ -432,10 +432,24 @@ int validate_params(const sar_radar_params *p) {
     return SAR_OK;
 }
 
+// Shape checks of the reconstruction points that need no device (the point
+// values are checked while the tiles are built).
+int validate_grid(const sar_grid *g) {
+    if (!g) return SAR_EINVAL;
+    if (g->pixels_xy == nullptr) {
+        if (g->nx <= 0 || g->ny <= 0 || (int64_t)g->nx * g->ny > (int64_t)1 << 30) return SAR_EINVAL;
+        if (!std::isfinite(g->x0) || !std::isfinite(g->y0) || !std::isfinite(g->dx) || !std::isfinite(g->dy))
+            return SAR_EINVAL;
+        return SAR_OK;
+    }
+    return (g->n_pixels <= 0 || g->n_pixels > (int64_t)1 << 30) ? SAR_EINVAL : SAR_OK;
+}
+
 int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t budget, sar_plan **out) {
     int rc = validate_params(params);
     if (rc) return rc;
-    if (!grid) return SAR_EINVAL;
+    rc = validate_grid(grid);
+    if (rc) return rc;
     sar_plan *pl = new (std::nothrow) sar_plan();
     if (!pl) return SAR_ENOMEM;
     pl->p = *params;

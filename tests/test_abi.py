@@ -97,6 +97,30 @@ def test_plan_parameters_rejected_without_gpu(lib):
         assert out.value is None
 
 
+def test_empty_or_invalid_grids_rejected_without_gpu(lib):
+    """An empty Cartesian grid, an empty point list, an oversized grid or a
+    non-finite grid origin gives SAR_EINVAL (1) before any CUDA call."""
+    import paper_2306_09784_gb300 as sar
+    lib.sar_plan_create.restype = ctypes.c_int
+    p = sar.RadarParams(f0=77e9, slope=1e9 / 102.4e-6, fs=128 / 102.4e-6, c=299792458.0,
+                        n_samples=128, os=4, n_rx=4, max_pulses=64, range_window=1, precision=0,
+                        kaiser_beta=0.0, phase_sign=1, crop_lo=0, crop_hi=0, time_origin=0,
+                        max_doppler_bins=0.0)
+    pts = (ctypes.c_double * 2)(0.0, 3.0)
+    bad = [dict(nx=0, ny=8), dict(nx=8, ny=0), dict(nx=-1, ny=8), dict(nx=1 << 16, ny=1 << 15),
+           dict(nx=8, ny=8, x0=float("nan")), dict(nx=8, ny=8, dx=float("inf")),
+           dict(pixels_xy=ctypes.cast(pts, ctypes.c_void_p), n_pixels=0),
+           dict(pixels_xy=ctypes.cast(pts, ctypes.c_void_p), n_pixels=-5)]
+    for kw in bad:
+        g = dict(x0=-1.0, y0=2.0, dx=0.05, dy=0.05, nx=8, ny=8, pixels_xy=None, n_pixels=0)
+        g.update(kw)
+        grid = sar.Grid(**g)
+        out = ctypes.c_void_p()
+        assert lib.sar_plan_create(ctypes.byref(p), ctypes.byref(grid), 0, ctypes.byref(out)) == 1, kw
+        assert out.value is None
+    assert lib.sar_plan_create(ctypes.byref(p), None, 0, ctypes.byref(out)) == 1
+
+
 def test_struct_layouts_match_header():
     import paper_2306_09784_gb300 as sar
     gcc = shutil.which("gcc")
