@@ -53,7 +53,7 @@ MUFU_LANES = 16
 # backprojection launch on this workload, from an ncu --set full capture of
 # the kernel source with this SHA-256 prefix (reported as null once the
 # kernel source differs).
-BP_TRAFFIC = {"sha256_16": "289609d5c491427a", "bytes": 33772032 + 3840}
+BP_TRAFFIC = {"sha256_16": "782954157b053083", "bytes": 33887488 + 5376}
 HBM_PEAK_FALLBACK_GBS = 6800.0
 
 

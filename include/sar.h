@@ -331,7 +331,9 @@ typedef struct sar_request {
     const float *w_az_host;   /* float [M] or NULL */
     const double *q_tx_host;  /* double [M][2] */
     const double *q_rx_host;  /* double [M][R][2] */
-    void *image_host;         /* complex64 [n_pixels] destination, or NULL (device only) */
+    void *image_host;         /* complex64 [n_pixels] destination, or NULL (device only); a
+                                 page-locked, mapped one is written by the final round's kernels,
+                                 any other by a copy after them */
 } sar_request;
 
 typedef struct sar_server_stats {

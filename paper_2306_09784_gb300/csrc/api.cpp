@@ -891,8 +891,9 @@ int sar_form_image_host(sar_plan *pl, const void *beat_host, int32_t M, const fl
     }
     if (!ok) return SAR_ECUDA;
     // A page-locked, mapped image_host (e.g. cudaHostAlloc memory under
-    // unified addressing) is written by the last chunk's kernels directly,
-    // tile by tile while they run, instead of by one copy after them.
+    // unified addressing) is written by the last chunk's kernels directly
+    // (next to the device image), tile by tile while they run, instead of by
+    // one copy after them.
     void *img_dev = nullptr;
     cudaPointerAttributes pa;
     if (cudaPointerGetAttributes(&pa, image_host) == cudaSuccess) {
@@ -1105,7 +1106,7 @@ namespace sar {
 // the 256-byte alignment of the profile block (rows keep their sample
 // alignment).
 int batch_add_rows(sar_batch *b, sar_plan *plan, const void *samples, const float *scales, int32_t M,
-                   const double *q_tx, const double *q_rx, void *image, int32_t accumulate) {
+                   const double *q_tx, const double *q_rx, void *image, int32_t accumulate, void *image_out) {
     if (!b || !plan || !samples || (plan->fp16 && !scales)) return SAR_EINVAL;
     if (b->n_jobs >= b->max_jobs || plan->device != b->device) return SAR_EINVAL;
     if (!q_tx || !q_rx || !image || M < 1 || M > plan->p.max_pulses) return SAR_EINVAL;
@@ -1120,6 +1121,7 @@ int batch_add_rows(sar_batch *b, sar_plan *plan, const void *samples, const floa
     if (rc) return rc;
     a.prof = samples;
     a.prof_scale = plan->fp16 ? scales : nullptr;
+    a.image_out = (float2 *)image_out;
     (void)smem;
     b->h_jobs[b->n_jobs] = a;
     b->units += a.units;

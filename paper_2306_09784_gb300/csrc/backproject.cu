@@ -680,7 +680,6 @@ __device__ __forceinline__ void process_segment(const BpArgs &a, const Smem &sm,
     }
 
     if (partial_dst == nullptr) {
-        float2 *dst = a.image_out ? a.image_out : a.image;
 #pragma unroll
         for (int j = 0; j < kPxPerThread; ++j) {
             if (oi[j] < 0) continue;
@@ -690,7 +689,8 @@ __device__ __forceinline__ void process_segment(const BpArgs &a, const Smem &sm,
                 v.x += o.x;
                 v.y += o.y;
             }
-            dst[oi[j]] = v;
+            a.image[oi[j]] = v;
+            if (a.image_out) a.image_out[oi[j]] = v;
         }
     } else {
 #pragma unroll
@@ -806,6 +806,7 @@ __global__ void __launch_bounds__(kFixupThreads) bp_batch_fixup_kernel(BpBatchAr
             v.y += old.y;
         }
         a.image[o] = v;
+        if (a.image_out) a.image_out[o] = v;
     }
 }
 
@@ -831,7 +832,6 @@ __global__ void __launch_bounds__(kFixupThreads) bp_fixup_kernel(BpArgs a) {
             acc[k].y += v.y;
         }
     }
-    float2 *dst = a.image_out ? a.image_out : a.image;
 #pragma unroll
     for (int k = 0; k < kFixupPx; ++k) {
         const int o = a.out_idx[(long long)tile * kTilePx + threadIdx.x + k * kFixupThreads];
@@ -842,7 +842,8 @@ __global__ void __launch_bounds__(kFixupThreads) bp_fixup_kernel(BpArgs a) {
             v.x += old.x;
             v.y += old.y;
         }
-        dst[o] = v;
+        a.image[o] = v;
+        if (a.image_out) a.image_out[o] = v;
     }
 }
 

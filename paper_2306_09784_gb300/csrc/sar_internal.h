@@ -60,7 +60,7 @@ struct BpArgs {
     const double *q_rx;        // [M][R][2]
     const float *fdopp;        // [n_pixels] or null
     float2 *image;             // [n_pixels]
-    float2 *image_out;         // where the result is written (null: image); may be mapped host memory
+    float2 *image_out;         // second destination of the result (null: none); may be mapped host memory
     float2 *partial;           // [G * seg_max][kTilePx]
     int *err;                  // device error flags
     const float2 *pix;         // [n_tiles][kTilePx] (dx, dy) from the tile reference
@@ -118,7 +118,8 @@ cudaError_t launch_backproject_batch(const BpBatchArgs &b, int rg, bool fp16, in
 
 // Used by the server (serve.cpp).
 int batch_add_rows(sar_batch *b, sar_plan *plan, const void *samples, const float *scales, int32_t M,
-                   const double *q_tx, const double *q_rx, void *image, int32_t accumulate);
+                   const double *q_tx, const double *q_rx, void *image, int32_t accumulate,
+                   void *image_out = nullptr);
 int plan_geometry(const sar_plan *pl, int *n_rx, int *n_samples, int *n_bins, int *fp16, int64_t *n_pixels,
                   int *max_pulses);
 int fill_bp_args(const sar_plan *pl, const void *prof, int M, const double *q_tx, const double *q_rx,

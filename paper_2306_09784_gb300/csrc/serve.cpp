@@ -103,6 +103,7 @@ struct Request {
     size_t b_beat = 0, b_waz = 0, b_qtx = 0, b_qrx = 0, b_prof = 0, b_img = 0;
     int next_pulse = 0;
     bool joined = false;          // took part in a round (its range compression is ordered before)
+    void *img_host_dev = nullptr;  // image_host as a device address, if page-locked and mapped
     bool finishing = false;       // final round enqueued
     cudaEvent_t rc_ev = nullptr;  // range compression done
     cudaEvent_t ev = nullptr;     // last GPU work of this request
@@ -187,6 +188,18 @@ int start_request(sar_server *s, Request *q) {
     if (cudaEventCreateWithFlags(&q->rc_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming) != cudaSuccess)
         return SAR_ECUDA;
+    if (r.image_host) {
+        // a page-locked, mapped destination is written by the final round's
+        // kernels themselves (besides the device image), so the image does
+        // not wait for a copy behind other requests' uploads
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, r.image_host) == cudaSuccess) {
+            if (pa.type == cudaMemoryTypeHost && pa.devicePointer && (uintptr_t)pa.devicePointer % 8 == 0)
+                q->img_host_dev = pa.devicePointer;
+        } else {
+            cudaGetLastError();
+        }
+    }
     bool ok = cudaMemcpyAsync(q->d_beat, r.beat_host, (size_t)M * R * N * 8, cudaMemcpyHostToDevice, s->copy_s) ==
               cudaSuccess;
     if (r.w_az_host)
@@ -253,8 +266,10 @@ int launch_round(sar_server *s, std::vector<Request *> &work, bool *launched) {
         } else {
             samples = q->d_prof + rows0 * q->n_bins * 8;
         }
+        const bool final_round = m0 + cnt == q->r.M;
         rc = sar::batch_add_rows(b, q->r.plan, samples, scales, cnt, (const double *)q->d_qtx + 2 * m0,
-                                 (const double *)q->d_qrx + 2 * rows0, q->d_img, m0 > 0 ? 1 : 0);
+                                 (const double *)q->d_qrx + 2 * rows0, q->d_img, m0 > 0 ? 1 : 0,
+                                 final_round ? q->img_host_dev : nullptr);
         if (rc) return rc;
         q->next_pulse = m0 + cnt;
     }
@@ -272,7 +287,7 @@ int launch_round(sar_server *s, std::vector<Request *> &work, bool *launched) {
         if (q->next_pulse < q->r.M) continue;
         // final round of q: image back to the host (if wanted), then done
         q->finishing = true;
-        if (q->r.image_host) {
+        if (q->r.image_host && !q->img_host_dev) {
             if (cudaStreamWaitEvent(s->copy_s, s->round_ev[k], 0) != cudaSuccess) return SAR_ECUDA;
             if (cudaMemcpyAsync(q->r.image_host, q->d_img, (size_t)q->n_pixels * 8, cudaMemcpyDeviceToHost,
                                 s->copy_s) != cudaSuccess)

@@ -32,6 +32,14 @@ def _frame(wl, precision=0):
     return dict(wl=wl, beat=beat, w_az=w_az, plan=plan, alone=alone.cpu().numpy(), host=host)
 
 
+class _DeviceArray:
+    """A float32 view of device memory the library owns (CUDA array interface)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (ptr, False),
+                                         "version": 2}
+
+
 def _submit(srv, f):
     h = f["host"]
     return srv.submit(f["plan"], h["beat"], h["q_tx"], h["q_rx"], w_az=h["w_az"], image=h["image"])
@@ -58,6 +66,28 @@ def test_served_frame_equals_standalone_and_oracle():
     assert rel_l2(img, oracle_image(f["wl"], f["beat"], f["w_az"])) <= TOL_FP32
     assert srv.release(t) == sar.SAR_OK
     assert srv.poll(t)[0] == sar.SAR_ENOTFOUND
+    srv.close()
+
+
+def test_host_image_mapped_and_pageable_match_the_device_image():
+    """A pinned (mapped) destination is written by the final round's kernels,
+    a pageable one by a copy: both equal the device image sar_poll returns,
+    bit for bit."""
+    import torch
+    import paper_2306_09784_gb300 as sar
+    f = _frame(synth.make_workload("small"))
+    h = f["host"]
+    srv = sar.Server(hbm_budget=256 << 20, chunk_pulses=40)
+    for image in (torch.empty(f["plan"].n_pixels, dtype=torch.complex64).pin_memory(),
+                  torch.empty(f["plan"].n_pixels, dtype=torch.complex64)):
+        t = srv.submit(f["plan"], h["beat"], h["q_tx"], h["q_rx"], w_az=h["w_az"], image=image)
+        assert srv.wait(t, 60000) == sar.SAR_OK
+        rc, state, img_dev, _ = srv.poll(t)
+        assert rc == sar.SAR_OK and img_dev
+        dev = torch.as_tensor(_DeviceArray(img_dev, 2 * f["plan"].n_pixels), device="cuda")
+        assert np.array_equal(image.numpy().view(np.float32), dev.cpu().numpy())
+        assert rel_l2(image.numpy(), f["alone"]) < 1e-5
+        srv.release(t)
     srv.close()
 
 
