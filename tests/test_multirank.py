@@ -43,3 +43,16 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(1.25, 1) == 1.25
     assert bench.aggregate_rate(100, 2, 1, 1.0) == pytest.approx(2e-7)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    """Under torchrun the reference arm (the FP64 oracle on the host cores)
+    runs on rank 0 alone; other ranks exit 0 without work or output."""
+    import argparse
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    args = argparse.Namespace(gpus=2, steps=3, warmup=3, impl="reference")
+    assert bench.run_reference(args) == 0
+    assert capsys.readouterr().out == ""
