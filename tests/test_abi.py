@@ -65,6 +65,8 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.sar_range_compress(None, None, 1, None, None, None) == 1
     assert lib.sar_backproject(None, None, 1, None, None, None, None, 0, None) == 1
     assert lib.sar_plan_check_errors(None) == 1
+    lib.sar_alu_peaks.restype = ctypes.c_int
+    assert lib.sar_alu_peaks(None, None, None) == 1
 
 
 def test_plan_parameters_rejected_without_gpu(lib):
