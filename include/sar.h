@@ -86,7 +86,9 @@ enum sar_precision {
  *              kernels' work is the same.
  *  max_doppler_bins  bound on |f_doppler(p)| (in bins) of the Doppler
  *              offsets passed to sar_backproject; the staged bin windows are
- *              widened by it.  Offsets beyond the bound are clamped to it.
+ *              widened by it (0..64).  A pixel whose offset lies beyond the
+ *              bound (or is not finite) is left out of that call and the call
+ *              is flagged SAR_EBOUNDS (see sar_backproject).
  * The derived phase rate beta = f0 / (c a1) cycles per bin, a1 = slope N_fft
  * / (c fs) bins per metre, must lie in [1e-9, 1e9] (f0 / (B os) for a chirp
  * of bandwidth B; about 19 at 77 GHz, 1 GHz, os 4); sar_plan_create rejects
@@ -155,7 +157,9 @@ typedef struct sar_plan_info {
  * before any CUDA call, for invalid parameters, a null or empty grid (nx or
  * ny < 1, n_pixels < 1 for a point list), more than 2^30 points or a
  * non-finite Cartesian origin or spacing; non-finite listed points give
- * SAR_EINVAL too.
+ * SAR_EINVAL too.  The first plan on a device also sets up the static scratch
+ * of sar_backproject_noalloc there (16 MiB of device memory, outside the
+ * budget, held until exit; SAR_ENOMEM if the device cannot provide it).
  */
 int sar_plan_create(const sar_radar_params *params, const sar_grid *grid,
                     size_t hbm_budget_bytes, sar_plan **out);
@@ -207,11 +211,16 @@ int sar_range_spectrum(sar_plan *plan, const void *beat_dev, int32_t M,
  *  q_tx_dev        double [M][2] Tx positions
  *  q_rx_dev        double [M][R][2] Rx positions
  *  fdopp_idx_dev   float [n_pixels] Doppler index offsets f_doppler(p) in bins
- *                  (f_doppler of Alg. 2), or NULL for none
+ *                  (f_doppler of Alg. 2, e.g. from sar_doppler_offsets), or
+ *                  NULL for none; needs a plan with max_doppler_bins > 0
  *  image_dev       complex64 [n_pixels]; written (accumulate = 0) or added to
  *                  (accumulate = 1, for sub-aperture accumulation)
  * Errors: SAR_EINVAL; non-finite or absurd geometry (beyond 1e6 m) is
- * skipped and flagged for sar_plan_check_errors (SAR_EBOUNDS).
+ * skipped and flagged for sar_plan_check_errors (SAR_EBOUNDS).  A pixel
+ * whose |f_doppler(p)| exceeds the plan's max_doppler_bins, or is not finite,
+ * gets no contribution from the call (its value is written as 0, or left
+ * unchanged when accumulating) and the call is flagged SAR_EBOUNDS too: its
+ * interpolation index would leave the staged bin window.
  */
 int sar_backproject(sar_plan *plan, const void *prof_dev, int32_t M,
                     const double *q_tx_dev, const double *q_rx_dev,
@@ -227,21 +236,24 @@ int sar_backproject(sar_plan *plan, const void *prof_dev, int32_t M,
  *
  * Same arguments, result and errors as sar_backproject.  The plan's
  * read-only tables are still used; only the scratch for tiles that several
- * CTAs share (partial sums, up to 8 KB per CTA and tile) comes from one
- * static 16 MiB device array in the library, which every GPU that loads the
- * library holds until the process exits.
- *  - A call whose work would need more than those 16 MiB returns
- *    SAR_ESCRATCH and enqueues nothing (a 1024 x 1024 image needs ~12.5 MB on
- *    a 152-SM GPU; about 1300 tiles of 32 x 32 points fit).
- *  - The first call on a device looks up the array's device address (a
- *    runtime symbol lookup, no allocation); make that first call before any
- *    stream capture.
+ * CTAs share (partial sums) comes from one static 16 MiB device array in the
+ * library: 2048 slots of 8 KB, one slot per pixel tile a CTA covers in part.
+ *  - sar_plan_create sets the array up on the plan's device: the first plan
+ *    on a device looks up its address, and that lookup makes the driver load
+ *    the library module holding it, which reserves its 16 MiB of device
+ *    memory (outside the plan's HBM budget) until the process exits.  The
+ *    imaging call itself makes no cudaMalloc, cudaFree or other allocating
+ *    call.  After a cudaDeviceReset, plans made before it must not be used
+ *    (their own device memory is gone as well) and this call is unsupported.
+ *  - A launch needs G x seg_max slots (G persistent CTAs, seg_max tiles per
+ *    CTA range); a call needing more than 2048 returns SAR_ESCRATCH and
+ *    enqueues nothing.  Example: a 1024 x 1024 image at 2048 chirps on 152 SMs
+ *    x 2 CTAs uses 304 x 5 = 1520 slots (12.5 MB).
  *  - Every call on a device shares the one array and finds the previous
  *    call's contents there; nothing in it needs to start at zero (each slot
  *    read is written earlier in the same call).  Calls whose work overlaps on
  *    the GPU (several streams, several host threads) race on it: serialise
  *    them.
- *  - The call itself makes no cudaMalloc, cudaFree or other allocating call.
  */
 int sar_backproject_noalloc(sar_plan *plan, const void *prof_dev, int32_t M,
                             const double *q_tx_dev, const double *q_rx_dev,

@@ -516,6 +516,13 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
         return SAR_ECUDA;
     }
     pl->num_sms = prop.multiProcessorCount;
+    // set-up of sar_backproject_noalloc's static scratch on this device (its
+    // module load reserves 16 MiB here, never in the imaging call)
+    rc = noalloc_setup(pl->device);
+    if (rc) {
+        delete pl;
+        return rc;
+    }
     if (bp_prepare(pl->fp16, pl->rg, pl->bp_smem) != cudaSuccess ||
         bp_occupancy(pl->fp16, pl->rg, pl->bp_smem, pl->minb, &pl->ctas_per_sm) != 0 || pl->ctas_per_sm < 1) {
         cudaGetLastError();

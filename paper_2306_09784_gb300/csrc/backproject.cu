@@ -288,7 +288,7 @@ __device__ __forceinline__ void prep_exact(const BpArgs &a, const Smem &sm, cons
         } else {
             q.x = __float_as_int((float)kGuardBins);
             q.z = -(1 << 30);
-            atomicOr(a.err, 1);
+            atomicOr(a.err, kErrGeometry);
         }
         q.y = (int)addr_c;
         pr[task] = q;
@@ -613,7 +613,16 @@ __device__ __forceinline__ void process_segment(const BpArgs &a, const Smem &sm,
         dy[j] = d.y;
         hd2[j] = 0.5f * fmaf(d.x, d.x, d.y * d.y);
         fdi[j] = 0.f;
-        if (FD && oi[j] >= 0) fdi[j] = fminf(fmaxf(a.fdopp[oi[j]], -a.fd_max), a.fd_max);
+        if (FD && oi[j] >= 0) {
+            // an offset beyond the plan's bound (or not finite) would index
+            // outside the staged window: the pixel is left out of this call
+            // (its sum is zeroed below) and the call is flagged
+            const float f = a.fdopp[oi[j]];
+            if (fabsf(f) <= a.fd_max)
+                fdi[j] = f;
+            else
+                atomicOr(a.err, kErrDopplerBound);
+        }
         acc_re[j] = 0.f;
         acc_im[j] = 0.f;
     }
@@ -672,8 +681,11 @@ __device__ __forceinline__ void process_segment(const BpArgs &a, const Smem &sm,
             cyc -= rintf(cyc);
             float sn, cs;
             sincospif(-2.0f * a.sign * cyc, &sn, &cs);
-            const float re = acc_re[j] * cs - acc_im[j] * sn;
-            const float im = acc_re[j] * sn + acc_im[j] * cs;
+            float re = acc_re[j] * cs - acc_im[j] * sn;
+            float im = acc_re[j] * sn + acc_im[j] * cs;
+            // out-of-bound offset (re-read rather than kept in a register
+            // through the pulse loop): no contribution from this call
+            if (oi[j] >= 0 && !(fabsf(a.fdopp[oi[j]]) <= a.fd_max)) re = im = 0.f;
             acc_re[j] = re;
             acc_im[j] = im;
         }

@@ -18,6 +18,9 @@ constexpr int kPxPerThread = kTilePx / kBpThreads;
 constexpr int kGuardBins = 2;
 // Absolute distances beyond this (m) are treated as invalid geometry.
 constexpr double kMaxRange = 1.0e6;
+// Bits of the device error flag (any bit set: SAR_EBOUNDS).
+constexpr int kErrGeometry = 1;      // non-finite or out-of-range antenna geometry
+constexpr int kErrDopplerBound = 2;  // |f_doppler(p)| beyond the plan's bound, or not finite
 
 // Range compression output modes.
 enum RcMode { kRcProfileF32 = 0, kRcProfileF16 = 1, kRcSpectrum = 2 };
@@ -127,6 +130,7 @@ int fill_bp_args(const sar_plan *pl, const void *prof, int M, const double *q_tx
 
 // Used by sar_backproject_noalloc (noalloc.cu).
 int plan_device(const sar_plan *pl);
+int noalloc_setup(int dev);  // once per device, at plan creation (device current)
 int backproject_with_scratch(sar_plan *pl, const void *prof, int M, const double *q_tx, const double *q_rx,
                              const float *fd, void *image, int accumulate, float2 *scratch, size_t scratch_bytes,
                              cudaStream_t s);

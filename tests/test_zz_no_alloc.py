@@ -9,8 +9,10 @@ CTAs) is one static 16 MiB device array that every call on a device shares.
 
 Through the C ABI these tests check that its image equals sar_backproject's,
 within the parity tolerance, on two calls in a row (the second call finds the
-first call's scratch contents), and that work beyond the static scratch is
-rejected with SAR_ESCRATCH.  This file is collected last on purpose.
+first call's scratch contents) -- plain, accumulating onto a filled image and
+with per-pixel Doppler offsets -- that a call leaves the device's free memory
+unchanged, and that work beyond the static scratch is rejected with
+SAR_ESCRATCH.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -52,6 +54,86 @@ def test_noalloc_matches_backproject_twice(name, precision):
     ref, outs = _run_both(wl, beat, np.hanning(wl.n_pulses), precision)
     for out in outs:
         assert rel_l2(out, ref) <= TOL_FP32
+
+
+def test_noalloc_accumulate_twice():
+    """accumulate = 1 onto a filled image: the fix-up's read-add-write path
+    through the static scratch equals sar_backproject's on the same image."""
+    import torch
+    import paper_2306_09784_gb300 as sar
+    lib = sar.load_library()
+    wl = synth.make_workload("small")
+    beat = synth.workload_beat(wl)
+    plan = make_plan(wl, precision=1)
+    b, w, qt, qr = to_dev(wl, beat, np.hanning(wl.n_pulses))
+    M = wl.n_pulses
+    prof = plan.range_compress(b, w)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    base = torch.randn(plan.n_pixels, dtype=torch.complex64, device="cuda", generator=g)
+    ref = plan.backproject(prof, M, qt, qr, image=base.clone(), accumulate=True).cpu().numpy()
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        img = base.clone()
+        rc = lib.sar_backproject_noalloc(plan.handle, prof.data_ptr(), M, qt.data_ptr(),
+                                         qr.data_ptr(), None, img.data_ptr(), 1, stream)
+        assert rc == sar.SAR_OK, sar.status_string(rc)
+        torch.cuda.synchronize()
+        assert rel_l2(img.cpu().numpy(), ref) <= TOL_FP32
+    assert plan.check_errors() == sar.SAR_OK
+
+
+def test_noalloc_doppler_offsets_twice():
+    """Per-pixel Doppler index offsets (a plan with max_doppler_bins > 0)
+    through the static scratch equal sar_backproject's."""
+    import torch
+    import paper_2306_09784_gb300 as sar
+    lib = sar.load_library()
+    wl = synth.make_workload("small")
+    beat = synth.workload_beat(wl)
+    plan = make_plan(wl, max_doppler_bins=2.0)
+    b, w, qt, qr = to_dev(wl, beat, np.hanning(wl.n_pulses))
+    M = wl.n_pulses
+    prof = plan.range_compress(b, w)
+    rng = np.random.Generator(np.random.PCG64(11))
+    fd = torch.from_numpy(rng.uniform(-1.5, 1.5, plan.n_pixels).astype(np.float32)).cuda()
+    ref = plan.backproject(prof, M, qt, qr, fdopp=fd).cpu().numpy()
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        img = torch.full((plan.n_pixels,), complex(7.0, -7.0), dtype=torch.complex64, device="cuda")
+        rc = lib.sar_backproject_noalloc(plan.handle, prof.data_ptr(), M, qt.data_ptr(),
+                                         qr.data_ptr(), fd.data_ptr(), img.data_ptr(), 0, stream)
+        assert rc == sar.SAR_OK, sar.status_string(rc)
+        torch.cuda.synchronize()
+        assert rel_l2(img.cpu().numpy(), ref) <= TOL_FP32
+    assert plan.check_errors() == sar.SAR_OK
+
+
+def test_noalloc_call_leaves_free_memory_unchanged():
+    """The property in the name: on a freshly created plan (whose creation set
+    the static scratch up), a call changes the device's free memory by
+    nothing.  sar_backproject runs first so that its kernels are loaded."""
+    import torch
+    import paper_2306_09784_gb300 as sar
+    lib = sar.load_library()
+    wl = synth.make_workload("small")
+    beat = synth.workload_beat(wl)
+    plan = make_plan(wl)
+    b, w, qt, qr = to_dev(wl, beat, np.hanning(wl.n_pulses))
+    M = wl.n_pulses
+    prof = plan.range_compress(b, w)
+    ref = plan.backproject(prof, M, qt, qr)
+    img = torch.zeros(plan.n_pixels, dtype=torch.complex64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    torch.cuda.mem_get_info()
+    free0, _ = torch.cuda.mem_get_info()
+    rc = lib.sar_backproject_noalloc(plan.handle, prof.data_ptr(), M, qt.data_ptr(),
+                                     qr.data_ptr(), None, img.data_ptr(), 0, stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert rc == sar.SAR_OK, sar.status_string(rc)
+    assert free1 == free0, (free0, free1)
+    assert rel_l2(img.cpu().numpy(), ref.cpu().numpy()) <= TOL_FP32
 
 
 def test_noalloc_full_config_twice():
