@@ -53,9 +53,13 @@ def _bind(lib):
                                             dp, dp, dp, i, dp, dp, i]
     lib.oracle_matched_filter.argtypes = [d, d, d, d, i, i, i, i, dp, dp, dp, dp,
                                           dp, i, dp, dp, i]
+    lib.oracle_polar_grid.argtypes = [d, d, d, d, i, i, dp, d, d, d, d, d, ctypes.c_longlong, dp,
+                                      ctypes.POINTER(ctypes.c_longlong)]
+    lib.oracle_doppler_offsets.argtypes = [d, d, d, i, i, i, dp, dp, dp, i, dp, dp]
     for name in ("oracle_window", "oracle_dft", "oracle_fft", "oracle_range_compress",
                  "oracle_backproject", "oracle_backproject_alg1",
-                 "oracle_matched_filter", "oracle_threads", "oracle_version"):
+                 "oracle_matched_filter", "oracle_threads", "oracle_version",
+                 "oracle_polar_grid", "oracle_doppler_offsets"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -185,6 +189,36 @@ def matched_filter(radar, beat, w_r, q_tx, q_rx, px, w_az=None, sign: int = 1,
                                      _ptr(_f64(q_tx)), _ptr(_f64(q_rx)), _ptr(_f64(w_az)),
                                      len(px), _ptr(px), _ptr(out.view(np.float64)),
                                      threads), "oracle_matched_filter")
+    return out
+
+
+def polar_grid(radar, q_tx, box, factor: float = 2.5, lib=None) -> np.ndarray:
+    """Polar reconstruction grid of Sec. III-E inside box = (x_min, x_max,
+    y_min, y_max); returns float64 [P, 2] (rings by range, then angle)."""
+    lib = lib or load()
+    q = _f64(q_tx).reshape(-1, 2)
+    n = ctypes.c_longlong()
+    args = (radar.f0, radar.slope, radar.fs, radar.c, radar.n_samples, len(q), _ptr(q),
+            float(box[0]), float(box[1]), float(box[2]), float(box[3]), float(factor))
+    _check(lib.oracle_polar_grid(*args, 0, None, ctypes.byref(n)), "oracle_polar_grid")
+    out = np.empty((n.value, 2))
+    _check(lib.oracle_polar_grid(*args, n.value, _ptr(out), ctypes.byref(n)), "oracle_polar_grid")
+    return out
+
+
+def doppler_offsets(radar, q_tx, q_rx, vel, px, t0: float = 0.0, lib=None) -> np.ndarray:
+    """Per-pixel f_doppler(p) in bins (Alg. 2, Sec. III-D) from the mean
+    platform velocity vel [M, 2] and the mean antenna positions; the carrier
+    is the one at the transform's time origin t0 (samples)."""
+    lib = lib or load()
+    q = _f64(q_tx).reshape(-1, 2)
+    M = len(q)
+    qr = _f64(q_rx).reshape(M, -1, 2)
+    px = _f64(px).reshape(-1, 2)
+    out = np.empty(len(px))
+    _check(lib.oracle_doppler_offsets(carrier_at(radar, t0), radar.fs, radar.c, radar.n_fft, M,
+                                      qr.shape[1], _ptr(q), _ptr(qr), _ptr(_f64(vel).reshape(M, 2)),
+                                      len(px), _ptr(px), _ptr(out)), "oracle_doppler_offsets")
     return out
 
 

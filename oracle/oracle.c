@@ -351,3 +351,113 @@ API int oracle_matched_filter(double f0, double slope, double fs, double c, int 
     }
     return 0;
 }
+
+/*
+ * Polar reconstruction grid (Sec. III-E, Fig. 2).  The grid originates in the
+ * centre of the synthetic aperture; its spacing is the radar's resolution
+ * divided by `factor` (the paper uses 2.5).  The paper takes the resolution
+ * from a point spread function it does not print; the textbook values stand
+ * in for it:
+ *   range:   dr = c / (2 B), B = |slope| N / fs the swept bandwidth;
+ *   azimuth: lambda r / (2 L) at range r, i.e. the angle dphi = lambda / (2 L),
+ *            lambda = c / f_c at the sweep's centre frequency
+ *            f_c = f0 + slope N / (2 fs), L = |q_tx(M-1) - q_tx(0)|.
+ * With centre o = (q_tx(0) + q_tx(M-1)) / 2, along-track unit vector
+ * u = (q_tx(M-1) - q_tx(0)) / L and its left normal v = (-u_y, u_x), the
+ * grid points are
+ *   o + (k Dr) (cos(j Dphi) u + sin(j Dphi) v),  Dr = dr / factor,
+ *   Dphi = dphi / factor,  integers k >= 1 and j with j Dphi in [-pi, pi),
+ * and the ones kept lie in the box [x_min, x_max] x [y_min, y_max] (borders
+ * included), listed by ring k, then by angle j, both ascending.
+ * Every (k, j) pair is visited (plain enumeration).  out_xy may be NULL (count
+ * only); otherwise at most `capacity` points are written.  *n_out receives
+ * the number of grid points in the box.  Returns -1 for invalid input.
+ */
+API int oracle_polar_grid(double f0, double slope, double fs, double c, int N, int M,
+                          const double *q_tx, double x_min, double x_max, double y_min,
+                          double y_max, double factor, long long capacity, double *out_xy,
+                          long long *n_out) {
+    if (N <= 0 || M < 2 || !(factor > 0) || !(x_max >= x_min) || !(y_max >= y_min) || !n_out)
+        return -1;
+    const double ax = q_tx[2 * (M - 1)] - q_tx[0], ay = q_tx[2 * (M - 1) + 1] - q_tx[1];
+    const double L = hypot(ax, ay);
+    if (!(L > 0)) return -1;
+    const double ux = ax / L, uy = ay / L;
+    const double vx = -uy, vy = ux;
+    const double ox = 0.5 * (q_tx[0] + q_tx[2 * (M - 1)]);
+    const double oy = 0.5 * (q_tx[1] + q_tx[2 * (M - 1) + 1]);
+    const double B = fabs(slope) * N / fs;
+    const double fc = f0 + slope * N / (2.0 * fs);
+    const double dr = c / (2.0 * B) / factor;
+    const double dphi = (c / fc) / (2.0 * L) / factor;
+    /* the farthest box corner bounds the rings */
+    double rmax = 0.0;
+    const double cx[4] = {x_min, x_max, x_min, x_max}, cy[4] = {y_min, y_min, y_max, y_max};
+    for (int i = 0; i < 4; ++i) {
+        const double d = hypot(cx[i] - ox, cy[i] - oy);
+        if (d > rmax) rmax = d;
+    }
+    const long long kmax = (long long)floor(rmax / dr) + 1;
+    const long long jlo = (long long)ceil(-PI / dphi), jhi = (long long)ceil(PI / dphi) - 1;
+    long long n = 0;
+    for (long long k = 1; k <= kmax; ++k) {
+        const double r = k * dr;
+        for (long long j = jlo; j <= jhi; ++j) {
+            const double phi = j * dphi;
+            const double cs = cos(phi), sn = sin(phi);
+            const double x = ox + r * (cs * ux + sn * vx);
+            const double y = oy + r * (cs * uy + sn * vy);
+            if (x >= x_min && x <= x_max && y >= y_min && y <= y_max) {
+                if (out_xy && n < capacity) {
+                    out_xy[2 * n] = x;
+                    out_xy[2 * n + 1] = y;
+                }
+                ++n;
+            }
+        }
+    }
+    *n_out = n;
+    return 0;
+}
+
+/*
+ * Per-pixel Doppler index offsets f_doppler(p) of Alg. 2 (Sec. III-D): the
+ * radial velocity terms of Alg. 1 (lines 5, 8, 9, 11) evaluated once per pixel
+ * with the average vehicle velocity and the aperture's mean antenna
+ * positions instead of per chirp and antenna:
+ *   vbar = mean_m vel(m),  qt = mean_m q_tx(m),  qr = mean_{m,n} q_rx(m, n),
+ *   ddot(p) = -( <p - qt, vbar> / ||p - qt|| + <p - qr, vbar> / ||p - qr|| ),
+ *   f_doppler(p) = f0 ddot(p) / c * n_fft / fs   [bins].
+ * ddot is the rate of change of the two-way path d_tx + d_rx for a platform
+ * moving with vbar; under the beat model Rx conj(Tx) with the +j transform
+ * (the reading this oracle follows throughout) it shifts a target's beat
+ * frequency by f0 ddot / c, which is Alg. 1's f0 v / c with v the scene's
+ * velocity relative to the radar.  f0 is the carrier at the transform's time
+ * origin.  vel is the platform velocity per chirp [M][2].
+ */
+API int oracle_doppler_offsets(double f0, double fs, double c, int n_fft, int M, int R,
+                               const double *q_tx, const double *q_rx, const double *vel,
+                               int P, const double *px, double *out) {
+    if (M <= 0 || R <= 0 || P < 0 || n_fft <= 0) return -1;
+    double tx = 0, ty = 0, rx = 0, ry = 0, vx = 0, vy = 0;
+    for (int m = 0; m < M; ++m) {
+        tx += q_tx[2 * m];
+        ty += q_tx[2 * m + 1];
+        vx += vel[2 * m];
+        vy += vel[2 * m + 1];
+        for (int n = 0; n < R; ++n) {
+            rx += q_rx[2 * ((long long)m * R + n)];
+            ry += q_rx[2 * ((long long)m * R + n) + 1];
+        }
+    }
+    tx /= M; ty /= M; vx /= M; vy /= M;
+    rx /= (double)M * R; ry /= (double)M * R;
+    for (int p = 0; p < P; ++p) {
+        const double ex = px[2 * p] - tx, ey = px[2 * p + 1] - ty;
+        const double gx = px[2 * p] - rx, gy = px[2 * p + 1] - ry;
+        const double v_tx = (ex * vx + ey * vy) / hypot(ex, ey);
+        const double v_rx = (gx * vx + gy * vy) / hypot(gx, gy);
+        out[p] = f0 * (-(v_tx + v_rx)) / c * n_fft / fs;
+    }
+    return 0;
+}

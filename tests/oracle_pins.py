@@ -410,6 +410,231 @@ def pin_bp_matches_matched_filter(lib):
     assert rel_l2(img, ref) < 5e-3
 
 
+# --------------------------------------------------------------------------
+# polar reconstruction grid (Sec. III-E) and Doppler offsets (Sec. III-D)
+# --------------------------------------------------------------------------
+def _table1_radar(**kw):
+    """Table I: f0 76.6 GHz, B 931 MHz, T_P 102.4 us, PRI 106.7 us; fs 10 MHz."""
+    base = dict(f0=76.6e9, bandwidth=931e6, t_chirp=102.4e-6, pri=106.7e-6,
+                n_samples=1024, n_rx=1, os=4)
+    base.update(kw)
+    return synth.Radar(**base)
+
+
+def _ring_counts(o, r, box, dphi):
+    """Points of the angular lattice j dphi in [-pi, pi) on the circle of
+    radius r about o that lie in the box, counted from the circle-box
+    intersection (crossing angles of the four border lines), not by
+    enumerating the lattice."""
+    x0, x1, y0, y1 = box
+    cuts = [-math.pi, math.pi]
+    for xb in (x0, x1):
+        c = (xb - o[0]) / r
+        if abs(c) <= 1:
+            a = math.acos(c)
+            cuts += [a, -a]
+    for yb in (y0, y1):
+        sn = (yb - o[1]) / r
+        if abs(sn) <= 1:
+            a = math.asin(sn)
+            cuts += [a, math.pi - a if a > 0 else -math.pi - a]
+    cuts = sorted(min(max(c, -math.pi), math.pi) for c in cuts)
+    n = 0
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        if b - a < 1e-15:
+            continue
+        m = 0.5 * (a + b)
+        x, y = o[0] + r * math.cos(m), o[1] + r * math.sin(m)
+        if x0 <= x <= x1 and y0 <= y <= y1:
+            jlo = max(math.ceil(a / dphi), math.ceil(-math.pi / dphi))
+            jhi = min(math.floor(b / dphi), math.ceil(math.pi / dphi) - 1)
+            n += max(0, jhi - jlo + 1)
+    return n
+
+
+def _polar_setup(speed=8.0, M=1024):
+    radar = _table1_radar()
+    q_tx, _ = synth.trajectory(radar, M, speed=speed)
+    o = 0.5 * (q_tx[0] + q_tx[-1])
+    L = float(np.hypot(*(q_tx[-1] - q_tx[0])))
+    lam = C0 / (radar.f0 + radar.bandwidth / 2.0)
+    dr = C0 / (2.0 * radar.bandwidth) / 2.5
+    dphi = lam / (2.0 * L) / 2.5
+    return radar, q_tx, o, L, dr, dphi
+
+
+def pin_polar_grid_lattice(lib):
+    """Every point sits on the lattice (k dr, j dphi) about the aperture centre
+    with dr = c / (2 B) / 2.5 and dphi = lambda / (2 L) / 2.5 (Table I: 6.44 cm),
+    inside the box, once, ring by ring with ascending angle; and per ring the
+    count equals the number of lattice angles inside the circle-box
+    intersection computed from the crossing angles."""
+    radar, q_tx, o, L, dr, dphi = _polar_setup()
+    assert abs(dr - 0.0644022) < 1e-7
+    box = (-3.31, 2.93, 1.07, 6.13)
+    g = oracle.polar_grid(radar, q_tx, box, 2.5, lib=lib)
+    assert len(g) > 1000
+    assert np.all((g[:, 0] >= box[0]) & (g[:, 0] <= box[1]) & (g[:, 1] >= box[2]) & (g[:, 1] <= box[3]))
+    e = g - o
+    k = np.hypot(e[:, 0], e[:, 1]) / dr
+    j = np.arctan2(e[:, 1], e[:, 0]) / dphi
+    assert np.max(np.abs(k - np.rint(k))) < 1e-9
+    assert np.max(np.abs(j - np.rint(j))) < 1e-6
+    ki, ji = np.rint(k).astype(np.int64), np.rint(j).astype(np.int64)
+    assert ki.min() >= 1
+    key = ki * 10 ** 7 + ji
+    assert np.all(np.diff(key) > 0)  # unique, rings ascending, angles ascending
+    for kk in range(1, int(ki.max()) + 2):
+        assert int(np.sum(ki == kk)) == _ring_counts(o, kk * dr, box, dphi), kk
+
+
+def pin_polar_grid_spacing(lib):
+    """Neighbours on a ring are lambda r / (2 L) / 2.5 apart (chord 2 r sin(dphi/2))
+    and neighbouring rings dr apart: the textbook range and azimuth
+    resolutions divided by the factor; a factor of 5 doubles the density
+    along both axes (4x the points)."""
+    radar, q_tx, o, L, dr, dphi = _polar_setup(speed=9.0)
+    box = (-1.5, 1.5, 4.0, 7.0)
+    g = oracle.polar_grid(radar, q_tx, box, 2.5, lib=lib)
+    e = g - o
+    r = np.hypot(e[:, 0], e[:, 1])
+    ring = np.rint(r / dr).astype(np.int64)
+    kk = int(np.median(ring))
+    pts = g[ring == kk]
+    d = np.hypot(*np.diff(pts, axis=0).T)
+    lam = C0 / (radar.f0 + radar.bandwidth / 2.0)
+    az = lam * (kk * dr) / (2.0 * L) / 2.5
+    assert np.allclose(d, 2 * kk * dr * math.sin(dphi / 2), rtol=1e-9)
+    assert abs(np.median(d) / az - 1.0) < 1e-4
+    g5 = oracle.polar_grid(radar, q_tx, box, 5.0, lib=lib)
+    assert abs(len(g5) / len(g) - 4.0) < 0.05
+
+
+def pin_polar_grid_point_target(lib):
+    """A point target on a grid point images to its peak exactly there; one
+    between grid points peaks at one of the four lattice points around it."""
+    radar = _radar(n_samples=128, n_rx=2, os=4)
+    M = 96
+    q_tx, q_rx = synth.trajectory(radar, M)
+    box = (-0.45, 0.52, 3.61, 4.33)
+    g = oracle.polar_grid(radar, q_tx, box, 2.5, lib=lib)
+    o = 0.5 * (q_tx[0] + q_tx[-1])
+    L = float(np.hypot(*(q_tx[-1] - q_tx[0])))
+    dr = C0 / (2.0 * radar.bandwidth) / 2.5
+    dphi = C0 / (radar.f0 + radar.bandwidth / 2.0) / (2.0 * L) / 2.5
+    w_r = oracle.window(oracle.WINDOW_HANN, radar.n_samples, lib=lib)
+    wa = np.hanning(M)
+    on = g[int(np.argmin(np.hypot(g[:, 0] - 0.03, g[:, 1] - 3.97)))]
+    r0, p0 = math.hypot(*(on - o)), math.atan2(*(on - o)[::-1])
+    off = o + (r0 + 0.43 * dr) * np.array([math.cos(p0 + 0.61 * dphi), math.sin(p0 + 0.61 * dphi)])
+    for tgt, on_grid in ((on, True), (off, False)):
+        beat = synth.beat_signal(radar, q_tx, q_rx, tgt[None, :], np.array([1.0 + 0.2j]))
+        S = oracle.range_compress(beat, w_r, radar.os, lib=lib)
+        img = oracle.backproject(radar, S, q_tx, q_rx, g, w_az=wa, lib=lib)
+        best = g[int(np.argmax(np.abs(img)))]
+        if on_grid:
+            assert np.allclose(best, tgt, atol=1e-12)
+        else:
+            e = best - o
+            kb, jb = math.hypot(*e) / dr, math.atan2(e[1], e[0]) / dphi
+            kt, jt = (r0 + 0.43 * dr) / dr, (p0 + 0.61 * dphi) / dphi
+            assert round(kb) in (math.floor(kt), math.ceil(kt)), (kb, kt)
+            assert round(jb) in (math.floor(jt), math.ceil(jt)), (jb, jt)
+
+
+def pin_doppler_offsets_closed_form(lib):
+    """Track along +x at speed v: a pixel ahead on the track axis closes at
+    2 v, f_doppler = -2 f0 v / c * N_fft / fs bins; one behind opens at 2 v;
+    one abeam of the mean Tx position sees only the Rx offset's share,
+    f0 v dx / (c r) * N_fft / fs with dx the mean Rx offset along x."""
+    radar = _radar(n_samples=256, n_rx=3, os=4)
+    M, v = 65, 12.0
+    q_tx, q_rx = synth.trajectory(radar, M, speed=v)
+    vel = np.tile([v, 0.0], (M, 1))
+    px = np.array([[40.0, 0.0], [-40.0, 0.0], [0.0, 7.0]])
+    fd = oracle.doppler_offsets(radar, q_tx, q_rx, vel, px, lib=lib)
+    scale = radar.f0 / C0 * radar.n_fft / radar.fs
+    assert abs(fd[0] - (-2 * v * scale)) < 1e-9 * abs(fd[0])
+    assert abs(fd[1] - (2 * v * scale)) < 1e-9 * abs(fd[1])
+    dx = float(np.mean(q_rx[..., 0]) - np.mean(q_tx[:, 0]))
+    gx = -dx
+    ref = -(v * gx / math.hypot(gx, 7.0)) * scale
+    assert abs(fd[2] - ref) < 1e-9 * abs(ref)
+
+
+def pin_doppler_offsets_finite_difference(lib):
+    """The offset equals f0 / c times the rate of change of the two-way path
+    to the aperture's middle chirp, taken as a central difference of the
+    per-chirp distances (positions only, no velocity input) over one PRI, for
+    a straight constant-velocity track with an odd chirp count."""
+    radar = _radar(n_samples=128, n_rx=4, os=4)
+    M, v = 81, 9.5
+    q_tx, q_rx = synth.trajectory(radar, M, speed=v)
+    vel = np.tile([v, 0.0], (M, 1))
+    rng = np.random.Generator(np.random.PCG64(21))
+    px = np.stack([rng.uniform(-6, 6, 50), rng.uniform(1, 12, 50)], 1)
+    fd = oracle.doppler_offsets(radar, q_tx, q_rx, vel, px, lib=lib)
+    mc = M // 2
+    qr_mean = q_rx.mean(axis=1)
+
+    def path(m):
+        return np.hypot(*(px - q_tx[m]).T) + np.hypot(*(px - qr_mean[m]).T)
+
+    ddot = (path(mc + 1) - path(mc - 1)) / (2 * radar.pri)
+    ref = radar.f0 * ddot / C0 * radar.n_fft / radar.fs
+    assert np.max(np.abs(fd - ref)) < 1e-6 * np.max(np.abs(ref))
+
+
+def pin_doppler_offsets_refocus(lib):
+    """With the antennas moving during each chirp (intra-chirp motion, 20 m/s),
+    Alg. 2 with these per-pixel offsets focuses each target as the same scene
+    without motion does (|P| within 0.5 %); without offsets the focus drops
+    below 70 %, with reversed offsets below 15 %."""
+    radar = _radar(n_samples=128, n_rx=2, os=4)
+    M, v_p = 96, np.array([20.0, 0.0])
+    q_tx, q_rx = synth.trajectory(radar, M, speed=float(v_p[0]))
+    tg = np.array([[2.6, 1.5], [4.0, 2.5], [5.0, 3.75]])
+    am = np.array([1.0, 0.7 * np.exp(1j), 1.2j])
+    w_r = oracle.window(oracle.WINDOW_HANN, radar.n_samples, lib=lib)
+    wa = np.hanning(M)
+    moving = synth.beat_signal(radar, q_tx, q_rx, tg, am, intra_chirp_velocity=v_p)
+    still = synth.beat_signal(radar, q_tx, q_rx, tg, am)
+    S = oracle.range_compress(moving, w_r, radar.os, lib=lib)
+    S0 = oracle.range_compress(still, w_r, radar.os, lib=lib)
+    fd = oracle.doppler_offsets(radar, q_tx, q_rx, np.tile(v_p, (M, 1)), tg, lib=lib)
+    assert np.all(np.abs(fd) > 1.0)
+    focus = np.abs(oracle.backproject(radar, S0, q_tx, q_rx, tg, w_az=wa, lib=lib))
+    for f, lo, hi in ((fd, 0.995, 1.005), (None, 0.0, 0.7), (-fd, 0.0, 0.15)):
+        got = np.abs(oracle.backproject(radar, S, q_tx, q_rx, tg, w_az=wa, fd_idx=f, lib=lib))
+        assert np.all((got / focus >= lo) & (got / focus <= hi)), (got / focus, lo, hi)
+
+
+def pin_doppler_velocity_variation_below_100hz(lib):
+    """Sec. III-D: the velocity may be taken as constant over a chirp sequence
+    because its variation moves the Doppler frequency by well under 100 Hz.
+    Table I sequence (1024 chirps, 109.3 ms) of a car at 10 m/s accelerating
+    at 1 m/s^2: each chirp's own velocity moves every pixel's Doppler
+    frequency by at most 2 f0 max|v(m) - vbar| / c = 28 Hz, attained for a
+    pixel along the track."""
+    radar = _table1_radar(n_rx=2)
+    M = 1024
+    q_tx, q_rx = synth.trajectory(radar, M, speed=10.0)
+    t = (np.arange(M) - (M - 1) / 2) * radar.pri
+    vel = np.stack([10.0 + 1.0 * t, np.zeros(M)], 1)
+    rng = np.random.Generator(np.random.PCG64(4))
+    px = np.concatenate([[[60.0, 0.0]], np.stack([rng.uniform(-15, 15, 40), rng.uniform(1, 31, 40)], 1)])
+    hz = radar.fs / radar.n_fft
+    mean = oracle.doppler_offsets(radar, q_tx, q_rx, vel, px, lib=lib)
+    dev = 0.0
+    for m in (0, M // 3, M - 1):
+        per = oracle.doppler_offsets(radar, q_tx, q_rx, np.tile(vel[m], (M, 1)), px, lib=lib)
+        dev = max(dev, float(np.max(np.abs(per - mean))) * hz)
+    bound = 2 * radar.f0 * float(np.max(np.abs(vel[:, 0] - vel[:, 0].mean()))) / C0
+    assert abs(bound - 28.0) < 0.5, bound
+    assert abs(dev - bound) < 1e-6 * bound, (dev, bound)
+    assert dev < 100.0
+
+
 ALL_PINS = [
     pin_fft, pin_windows, pin_range_compress, pin_matched_filter_closed_form,
     pin_backproject_point_target, pin_time_origin_mid_bin, pin_interpolation_convergence,
@@ -417,4 +642,7 @@ ALL_PINS = [
     pin_linearity, pin_alg1_equals_alg2, pin_alg1_doppler_sign, pin_rx_halving, pin_single_term,
     pin_subaperture_additivity, pin_translation_invariance,
     pin_bp_matches_matched_filter,
+    pin_polar_grid_lattice, pin_polar_grid_spacing, pin_polar_grid_point_target,
+    pin_doppler_offsets_closed_form, pin_doppler_offsets_finite_difference,
+    pin_doppler_offsets_refocus, pin_doppler_velocity_variation_below_100hz,
 ]

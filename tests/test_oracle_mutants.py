@@ -68,6 +68,23 @@ MUTANTS = [
      "                const double *qr = q_rx + 2 * ((long long)m * R + n);\n"
      "                const double d_rx = hypot(x - qr[0], y - qr[1]);\n"
      "                const double d_hyp", None),
+    ("polar_range_resolution_halved", "const double dr = c / (2.0 * B) / factor;",
+     "const double dr = c / B / factor;", None),
+    ("polar_wavelength_at_f0", "const double fc = f0 + slope * N / (2.0 * fs);",
+     "const double fc = f0;", None),
+    ("polar_azimuth_resolution_full_aperture", "const double dphi = (c / fc) / (2.0 * L) / factor;",
+     "const double dphi = (c / fc) / L / factor;", None),
+    ("polar_origin_first_chirp", "const double ox = 0.5 * (q_tx[0] + q_tx[2 * (M - 1)]);",
+     "const double ox = q_tx[0];", None),
+    ("polar_half_circle", "jhi = (long long)ceil(PI / dphi) - 1;", "jhi = 0;", None),
+    ("doppler_sign", "out[p] = f0 * (-(v_tx + v_rx)) / c * n_fft / fs;",
+     "out[p] = f0 * (v_tx + v_rx) / c * n_fft / fs;", None),
+    ("doppler_rx_term_dropped", "out[p] = f0 * (-(v_tx + v_rx)) / c * n_fft / fs;",
+     "out[p] = f0 * (-(2.0 * v_tx)) / c * n_fft / fs;", None),
+    ("doppler_rx_mean_per_chirp_only", "rx /= (double)M * R; ry /= (double)M * R;",
+     "rx /= M; ry /= M;", None),
+    ("doppler_bins_scale", "out[p] = f0 * (-(v_tx + v_rx)) / c * n_fft / fs;",
+     "out[p] = f0 * (-(v_tx + v_rx)) / c / fs;", None),
 ]
 
 CHILD = r"""
