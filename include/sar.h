@@ -131,6 +131,40 @@ typedef struct sar_grid {
 
 typedef struct sar_plan sar_plan;
 
+/*
+ * Polar reconstruction grid (paper Sec. III-E, Fig. 2), a point list for
+ * sar_grid.pixels_xy.  The grid originates in the centre of the synthetic
+ * aperture and is `factor` times finer than the radar's resolution in range
+ * and azimuth (the paper: 2.5, "larger than 2 to depict point targets").  The
+ * paper's point-spread function is not printed; the textbook resolutions
+ * stand in for it: range c / (2 B), B = |slope| n_samples / fs, and azimuth
+ * lambda r / (2 L) at range r, i.e. the angle lambda / (2 L), with lambda =
+ * c / (f0 + slope n_samples / (2 fs)) and L = |q_tx(M-1) - q_tx(0)|.  With
+ * o = (q_tx(0) + q_tx(M-1)) / 2, u the unit vector from q_tx(0) to
+ * q_tx(M-1) and v = u turned +90 degrees, the points are
+ *     o + (k Dr) (cos(j Dphi) u + sin(j Dphi) v),
+ *     Dr = c / (2 B) / factor,  Dphi = lambda / (2 L) / factor,
+ * for integers k >= 1 and j with j Dphi in [-pi, pi), kept where they fall in
+ * the box [x_min, x_max] x [y_min, y_max] (borders included), listed by k then
+ * j, both ascending.
+ */
+typedef struct sar_polar_spec {
+    double x_min, x_max, y_min, y_max;  /* region of interest, m */
+    double factor;                      /* resolution / spacing (> 0) */
+} sar_polar_spec;
+
+/*
+ *  params     f0, slope, fs, c and n_samples are used
+ *  q_tx_host  double [M][2] Tx positions of the aperture (M >= 2, host)
+ *  xy_host    double [capacity][2] output (host), or NULL to count only
+ *  n_points   receives the number of grid points in the box
+ * Host-only (no device work).  SAR_EINVAL for invalid parameters, a
+ * zero-length aperture, an empty or non-finite box, or capacity below the
+ * count (then nothing beyond capacity is written; *n_points is the count).
+ */
+int sar_polar_grid(const sar_radar_params *params, const double *q_tx_host, int32_t M,
+                   const sar_polar_spec *spec, double *xy_host, int64_t capacity, int64_t *n_points);
+
 /* Sizes derived by a plan (all read-only). */
 typedef struct sar_plan_info {
     int32_t n_fft;              /* N * os */
@@ -226,6 +260,28 @@ int sar_backproject(sar_plan *plan, const void *prof_dev, int32_t M,
                     const double *q_tx_dev, const double *q_rx_dev,
                     const float *fdopp_idx_dev, void *image_dev,
                     int32_t accumulate, void *stream);
+
+/*
+ * Per-pixel Doppler index offsets f_doppler(p) of Alg. 2 (paper Sec. III-D):
+ * the velocity terms of Alg. 1 (lines 5, 8, 9 and the f0 v / c term of line
+ * 11) computed once per reconstruction point from the average vehicle
+ * velocity over the chirp sequence:
+ *     vbar = mean_m vel(m),  qt = mean_m q_tx(m),  qr = mean_{m,r} q_rx(m, r),
+ *     f_doppler(p) = -(f0' / c) (<p - qt, vbar> / |p - qt| + <p - qr, vbar> / |p - qr|) N_fft / fs
+ * in bins, f0' the carrier at the transform's time origin.  The bracket is
+ * minus the rate of change of the two-way path for a platform moving with
+ * vbar (a platform closing on p lowers the beat frequency under the beat
+ * model Rx conj(Tx); the same offset holds for the conjugate convention).
+ *  q_tx_dev   double [M][2], q_rx_dev double [M][R][2] (the frame's trajectory)
+ *  vel_dev    double [M][2] platform velocity per chirp (m/s)
+ *  fdopp_idx_dev  float [n_pixels] output in image order, ready for
+ *             sar_backproject; |f_doppler| <= 2 f0' |vbar| N_fft / (c fs), so a
+ *             plan with max_doppler_bins at least that takes every pixel
+ * Asynchronous on `stream` (two kernels, device memory only).  SAR_EINVAL for
+ * null or misaligned pointers or M outside 1..max_pulses.
+ */
+int sar_doppler_offsets(sar_plan *plan, const double *q_tx_dev, const double *q_rx_dev,
+                        const double *vel_dev, int32_t M, float *fdopp_idx_dev, void *stream);
 
 /*
  * sar_backproject without any device allocation on the library's side, for

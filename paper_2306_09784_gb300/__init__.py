@@ -31,7 +31,7 @@ EXPORTS = (
     "sar_batch_commit", "sar_batch_launch", "sar_batch_get_info",
     "sar_server_create", "sar_server_destroy", "sar_submit", "sar_poll", "sar_wait",
     "sar_release", "sar_server_get_stats", "sar_plan_autotune", "sar_plan_set_launch",
-    "sar_alu_peaks",
+    "sar_alu_peaks", "sar_polar_grid", "sar_doppler_offsets",
 )
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 
@@ -71,6 +71,11 @@ class PlanInfo(ctypes.Structure):
         ("cycles_per_bin", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
         ("rx_group", ctypes.c_int32), ("regs_ctas_per_sm", ctypes.c_int32),
     ]
+
+
+class PolarSpec(ctypes.Structure):
+    _fields_ = [("x_min", ctypes.c_double), ("x_max", ctypes.c_double), ("y_min", ctypes.c_double),
+                ("y_max", ctypes.c_double), ("factor", ctypes.c_double)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -139,6 +144,9 @@ def load_library(path: str = LIB_PATH):
     lib.sar_version.argtypes = []
     dptr = ctypes.POINTER(ctypes.c_double)
     lib.sar_alu_peaks.argtypes = [dptr, dptr, dptr]
+    lib.sar_polar_grid.argtypes = [ctypes.POINTER(RadarParams), vp, i32, ctypes.POINTER(PolarSpec), vp,
+                                   ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    lib.sar_doppler_offsets.argtypes = [vp, vp, vp, vp, i32, vp, vp]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("sar_plan_destroy", "sar_status_string", "sar_batch_destroy",
@@ -156,6 +164,25 @@ def alu_peaks() -> dict:
     _check(lib.sar_alu_peaks(ctypes.byref(f), ctypes.byref(f2), ctypes.byref(m)), "sar_alu_peaks")
     return {"fma_lane_ops_per_s": f.value, "ffma2_lane_ops_per_s": f2.value,
             "mufu_ops_per_s": m.value}
+
+
+def polar_grid(radar, q_tx, box, factor: float = 2.5):
+    """Polar reconstruction grid of Sec. III-E (sar_polar_grid) for a
+    synth.Radar-like object, the aperture's Tx positions q_tx [M, 2] (host)
+    and box = (x_min, x_max, y_min, y_max); returns float64 numpy [P, 2]."""
+    import numpy as np
+    lib = load_library()
+    p = RadarParams(f0=radar.f0, slope=radar.slope, fs=radar.fs, c=radar.c,
+                    n_samples=radar.n_samples)
+    q = np.ascontiguousarray(q_tx, dtype=np.float64).reshape(-1, 2)
+    spec = PolarSpec(*(float(v) for v in box), float(factor))
+    n = ctypes.c_int64()
+    _check(lib.sar_polar_grid(ctypes.byref(p), q.ctypes.data, len(q), ctypes.byref(spec), None, 0,
+                              ctypes.byref(n)), "sar_polar_grid")
+    out = np.empty((n.value, 2))
+    _check(lib.sar_polar_grid(ctypes.byref(p), q.ctypes.data, len(q), ctypes.byref(spec),
+                              out.ctypes.data, n.value, ctypes.byref(n)), "sar_polar_grid")
+    return out
 
 
 def status_string(status: int) -> str:
@@ -304,6 +331,22 @@ class Plan:
                                          _ptr(fdopp), _ptr(image), 1 if accumulate else 0,
                                          _stream(stream)), "sar_backproject")
         return image
+
+    def doppler_offsets(self, q_tx, q_rx, vel, out=None, stream=None):
+        """Per-pixel f_doppler(p) in bins from the mean platform velocity
+        (sar_doppler_offsets): q_tx [M, 2], q_rx [M, R, 2], vel [M, 2] float64
+        CUDA tensors -> float32 [n_pixels] in image order."""
+        import torch
+        _require_cuda(q_tx, "q_tx", torch.float64)
+        _require_cuda(q_rx, "q_rx", torch.float64)
+        _require_cuda(vel, "vel", torch.float64)
+        if out is None:
+            out = torch.empty(self.n_pixels, dtype=torch.float32, device=q_tx.device)
+        _require_cuda(out, "out", torch.float32)
+        _check(self._lib.sar_doppler_offsets(self._plan, _ptr(q_tx), _ptr(q_rx), _ptr(vel),
+                                             q_tx.shape[0], _ptr(out), _stream(stream)),
+               "sar_doppler_offsets")
+        return out
 
     def form_image_host(self, beat, q_tx, q_rx, image, w_az=None, stream=None):
         """Whole frame from host tensors (pinned for speed); blocks until done."""

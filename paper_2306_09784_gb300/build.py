@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libsar.so")
-SOURCES = ["api.cpp", "serve.cpp", "range_compress.cu", "backproject.cu", "noalloc.cu", "peaks.cu"]
+SOURCES = ["api.cpp", "serve.cpp", "polar.cpp", "range_compress.cu", "backproject.cu", "doppler.cu",
+           "noalloc.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
           "-I", os.path.join(os.path.dirname(HERE), "include")]

@@ -48,6 +48,7 @@ struct sar_plan {
     TileInfo *d_tiles = nullptr;
     float2 *d_partial = nullptr;
     int *d_err = nullptr;
+    double *d_means = nullptr;  // sar_doppler_offsets: mean positions and velocity
     // staging buffers of sar_form_image_host
     void *s_beat = nullptr;
     float *s_waz = nullptr;
@@ -571,6 +572,11 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
         pl->d_err = (int *)q;
         if (!rc && cudaMemset(q, 0, sizeof(int) * 4) != cudaSuccess) rc = SAR_ECUDA;
     }
+    if (!rc) {
+        void *q = nullptr;
+        rc = dev_alloc(pl, sizeof(double) * 8, &q);
+        pl->d_means = (double *)q;
+    }
     if (rc) {
         free_plan(pl);
         return rc;
@@ -827,6 +833,32 @@ int sar_backproject(sar_plan *pl, const void *prof_dev, int32_t M, const double 
     if (fdopp_idx_dev && !(pl->fd_max > 0)) return SAR_EINVAL;
     return bp_launch(pl, prof_dev, M, q_tx_dev, q_rx_dev, fdopp_idx_dev, image_dev, accumulate,
                      (cudaStream_t)stream);
+}
+
+int sar_doppler_offsets(sar_plan *pl, const double *q_tx_dev, const double *q_rx_dev, const double *vel_dev,
+                        int32_t M, float *fdopp_idx_dev, void *stream) {
+    if (!pl || !q_tx_dev || !q_rx_dev || !vel_dev || !fdopp_idx_dev || M < 1 || M > pl->p.max_pulses)
+        return SAR_EINVAL;
+    if (!aligned(q_tx_dev, 8) || !aligned(q_rx_dev, 8) || !aligned(vel_dev, 8) || !aligned(fdopp_idx_dev, 4))
+        return SAR_EINVAL;
+    DopplerArgs a{};
+    a.q_tx = q_tx_dev;
+    a.q_rx = q_rx_dev;
+    a.vel = vel_dev;
+    a.M = M;
+    a.R = pl->p.n_rx;
+    a.tiles = pl->d_tiles;
+    a.pix = pl->d_pix;
+    a.out_idx = pl->d_out;
+    a.n_tiles = pl->n_tiles;
+    a.means = pl->d_means;
+    // f0 at the transform's time origin (the carrier the phase correction uses)
+    const double f0 = pl->beta_frac * pl->p.c * pl->a1;
+    a.scale = f0 / pl->p.c * (double)pl->n_fft / pl->p.fs;
+    a.fd = fdopp_idx_dev;
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return SAR_ECUDA;
+    return launch_doppler_offsets(a, (cudaStream_t)stream) == cudaSuccess ? SAR_OK : SAR_ECUDA;
 }
 
 int sar_form_image_host(sar_plan *pl, const void *beat_host, int32_t M, const float *w_az_host,

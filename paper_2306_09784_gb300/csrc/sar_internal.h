@@ -119,6 +119,20 @@ cudaError_t bp_batch_prepare(int rg, bool fp16, size_t smem, int *ctas_per_sm);
 cudaError_t launch_backproject_batch(const BpBatchArgs &b, int rg, bool fp16, int total_tiles, size_t smem,
                                      cudaStream_t s);
 
+// Per-pixel Doppler offsets (doppler.cu).
+struct DopplerArgs {
+    const double *q_tx, *q_rx, *vel;  // [M][2], [M][R][2], [M][2]
+    int M, R;
+    const TileInfo *tiles;
+    const float2 *pix;
+    const int *out_idx;
+    int n_tiles;
+    double *means;  // [6] device scratch of the plan
+    double scale;   // f0 / c * N_fft / fs: bins per (m/s) of path rate
+    float *fd;      // [n_pixels] output in image order
+};
+cudaError_t launch_doppler_offsets(const DopplerArgs &a, cudaStream_t s);
+
 // Used by the server (serve.cpp).
 int batch_add_rows(sar_batch *b, sar_plan *plan, const void *samples, const float *scales, int32_t M,
                    const double *q_tx, const double *q_rx, void *image, int32_t accumulate,

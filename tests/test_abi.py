@@ -145,6 +145,8 @@ int main(void) {
          sizeof(sar_server_config), sizeof(sar_request), sizeof(sar_server_stats));
   P(sar_request, M) P(sar_request, w_az_host) P(sar_request, image_host)
   P(sar_server_config, chunk_pulses) P(sar_server_stats, rounds) P(sar_server_stats, pool_bytes)
+  printf("sar_polar_spec %zu\n", sizeof(sar_polar_spec));
+  P(sar_polar_spec, factor)
   return 0;
 }
 """
@@ -178,3 +180,5 @@ int main(void) {
     assert int(got["sar_server_config.chunk_pulses"]) == sar.ServerConfig.chunk_pulses.offset
     assert int(got["sar_server_stats.rounds"]) == sar.ServerStats.rounds.offset
     assert int(got["sar_server_stats.pool_bytes"]) == sar.ServerStats.pool_bytes.offset
+    assert int(got["sar_polar_spec"]) == ctypes.sizeof(sar.PolarSpec)
+    assert int(got["sar_polar_spec.factor"]) == sar.PolarSpec.factor.offset

@@ -407,16 +407,54 @@ def test_time_origin_chirp_centre_conjugate(torch, small):
     assert rel_l2(img, np.conj(oracle_image(wl, beat, w_az, t0=t0))) <= TOL_FP32
 
 
+def _moving_platform(radar, M, v_p):
+    q_tx, q_rx = synth.trajectory(radar, M, speed=float(v_p[0]))
+    return q_tx, q_rx, np.tile(v_p, (M, 1))
+
+
+def _library_doppler(plan, q_tx, q_rx, vel):
+    import torch as t
+    fd = plan.doppler_offsets(t.from_numpy(q_tx).cuda(), t.from_numpy(np.ascontiguousarray(q_rx)).cuda(),
+                              t.from_numpy(vel).cuda())
+    t.cuda.synchronize()
+    return fd.cpu().numpy()
+
+
+def test_doppler_offsets_vs_oracle(torch):
+    """sar_doppler_offsets (Sec. III-D, mean velocity, a CUDA kernel over the
+    plan's pixels) against the oracle's, pixel by pixel, on the 1024 x 1024
+    precision grid with a jittered, accelerating track, and on a point list;
+    also under the chirp-centre time origin (carrier at the centre)."""
+    import paper_2306_09784_gb300 as sar
+    wl = synth.make_workload("precision")
+    M = wl.n_pulses
+    t = (np.arange(M) - (M - 1) / 2) * wl.radar.pri
+    vel = np.stack([10.0 + 0.8 * t, 0.3 * np.sin(t * 20.0)], 1)
+    px = wl.grid.pixels()
+    for origin, t0 in ((sar.ORIGIN_FIRST_SAMPLE, 0.0),
+                       (sar.ORIGIN_CHIRP_CENTRE, (wl.radar.n_samples - 1) / 2.0)):
+        plan = make_plan(wl, precision=1, max_doppler_bins=8.0, time_origin=origin)
+        got = _library_doppler(plan, wl.q_tx, wl.q_rx, vel)
+        ref = oracle.doppler_offsets(wl.radar, wl.q_tx, wl.q_rx, vel, px, t0=t0)
+        assert np.max(np.abs(got - ref)) <= 2e-6 * np.max(np.abs(ref)), np.max(np.abs(got - ref))
+    rng = np.random.Generator(np.random.PCG64(3))
+    pts = np.stack([rng.uniform(-10, 10, 5000), rng.uniform(0.5, 25, 5000)], 1)
+    plan = make_plan(wl, precision=1, max_doppler_bins=8.0, pixels_xy=pts)
+    got = _library_doppler(plan, wl.q_tx, wl.q_rx, vel)
+    ref = oracle.doppler_offsets(wl.radar, wl.q_tx, wl.q_rx, vel, pts)
+    assert np.max(np.abs(got - ref)) <= 2e-6 * np.max(np.abs(ref))
+
+
 def test_doppler_offsets_refocus_a_moving_platform(torch):
     """Alg. 2's per-pixel f_doppler(p) on a scene recorded with the antennas
     moving during each chirp (20 m/s, targets ahead of the track, offsets of
-    2 to 4 bins).  With f_doppler(p) from the scene's velocity relative to the
-    radar at the aperture centre, the CUDA image matches the oracle and each
+    2 to 4 bins).  With f_doppler(p) from sar_doppler_offsets (mean velocity),
+    the CUDA image matches the oracle given the oracle's own offsets, and each
     target focuses as the same scene without motion does; without offsets, or
     with their sign reversed, the focus collapses."""
     radar = synth.Radar(n_samples=128, n_rx=2, os=4)
     M, v_p = 96, np.array([20.0, 0.0])
-    q_tx, q_rx = synth.trajectory(radar, M, speed=float(v_p[0]))
+    q_tx, q_rx, vel = _moving_platform(radar, M, v_p)
     grid = synth.Grid(x0=2.0, y0=1.0, dx=0.05, dy=0.05, nx=72, ny=64)
     cells = np.array([[12, 10], [40, 30], [60, 55]])
     targets = np.stack([grid.x0 + cells[:, 0] * grid.dx, grid.y0 + cells[:, 1] * grid.dy], 1)
@@ -427,21 +465,64 @@ def test_doppler_offsets_refocus_a_moving_platform(torch):
                                intra_chirp_velocity=v_p).astype(np.complex64)
     still = synth.beat_signal(radar, q_tx, q_rx, targets, amps).astype(np.complex64)
     w_az = np.hanning(M)
-    e = grid.pixels() - q_tx[M // 2]
-    fd = (2.0 * radar.f0 * (e @ -v_p) / np.hypot(e[:, 0], e[:, 1]) / radar.c
-          * radar.n_fft / radar.fs).astype(np.float32)
     plan = make_plan(wl, max_doppler_bins=8.0)
+    fd = _library_doppler(plan, q_tx, q_rx, vel)
+    fd_ref = oracle.doppler_offsets(radar, q_tx, q_rx, vel, grid.pixels())
+    assert np.max(np.abs(fd - fd_ref)) <= 2e-6 * np.max(np.abs(fd_ref))
     img = gpu_image(plan, wl, moving, w_az, fdopp=fd)
     img_none = gpu_image(plan, wl, moving, w_az)
     img_neg = gpu_image(plan, wl, moving, w_az, fdopp=-fd)
-    assert rel_l2(img, oracle_image(wl, moving, w_az, fd_idx=fd.astype(np.float64))) <= TOL_FP32
+    assert plan.check_errors() == 0
+    assert rel_l2(img, oracle_image(wl, moving, w_az, fd_idx=fd_ref)) <= TOL_FP32
     focus = oracle_image(wl, still, w_az)
-    for t in targets:
-        ix, iy = nearest_pixel(grid, t)
+    for tg in targets:
+        ix, iy = nearest_pixel(grid, tg)
         i = iy * grid.nx + ix
         assert abs(abs(img[i]) / abs(focus[i]) - 1.0) < 5e-3
         assert abs(img_none[i]) < 0.7 * abs(focus[i])
         assert abs(img_neg[i]) < 0.15 * abs(focus[i])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_moving_platform_on_polar_grid(torch, precision):
+    """Sec. III-D and III-E together: a moving-platform scene (intra-chirp
+    motion at 20 m/s) imaged on the polar grid from sar_polar_grid with
+    offsets from sar_doppler_offsets.  The library's grid equals the oracle's,
+    the CUDA image equals the oracle's (oracle grid, oracle offsets) and every
+    target, placed on a grid point, peaks exactly there."""
+    import paper_2306_09784_gb300 as sar
+    radar = synth.Radar(n_samples=128, n_rx=2, os=4)
+    M, v_p = 96, np.array([20.0, 0.0])
+    q_tx, q_rx, vel = _moving_platform(radar, M, v_p)
+    box = (2.03, 5.61, 0.97, 4.22)
+    grid_lib = sar.polar_grid(radar, q_tx, box)
+    grid_ref = oracle.polar_grid(radar, q_tx, box)
+    assert len(grid_lib) == len(grid_ref) > 5000
+    assert np.max(np.abs(grid_lib - grid_ref)) < 1e-9
+    want = np.array([[2.6, 1.5], [4.0, 2.5], [5.0, 3.75], [3.3, 3.9]])
+    k = [int(np.argmin(np.hypot(*(grid_ref - w).T))) for w in want]
+    targets = grid_ref[k]
+    amps = np.array([1.0, 0.7 * np.exp(1j), 1.2j, 0.8 - 0.3j])
+    moving = synth.beat_signal(radar, q_tx, q_rx, targets, amps,
+                               intra_chirp_velocity=v_p).astype(np.complex64)
+    w_az = np.hanning(M)
+    cart = synth.Grid(2.0, 0.95, 0.05, 0.05, 74, 67)  # covers the box: sets the crop only
+    wl = synth.Workload("polar", radar, M, cart, q_tx, q_rx, targets, amps, None, 0,
+                        synth.crop_for(radar, cart, q_tx, q_rx))
+    plan = make_plan(wl, precision=precision, pixels_xy=grid_lib, max_doppler_bins=8.0)
+    fd = _library_doppler(plan, q_tx, q_rx, vel)
+    fd_ref = oracle.doppler_offsets(radar, q_tx, q_rx, vel, grid_ref)
+    assert np.max(np.abs(fd - fd_ref)) <= 2e-6 * np.max(np.abs(fd_ref))
+    img = gpu_image(plan, wl, moving, w_az, fdopp=fd)
+    assert plan.check_errors() == 0
+    ref = oracle_image(wl, moving, w_az, px=grid_ref, fd_idx=fd_ref)
+    assert rel_l2(img, ref) <= (TOL_FP32 if precision == 0 else TOL_FP16)
+    e = grid_ref - 0.5 * (q_tx[0] + q_tx[-1])
+    r, ph = np.hypot(e[:, 0], e[:, 1]), np.arctan2(e[:, 1], e[:, 0])
+    for kk in k:  # the neighbourhood of each target: +-3 rings, +-6 angles
+        win = np.nonzero((np.abs(r - r[kk]) < 0.2) & (np.abs(ph - ph[kk]) < 0.03))[0]
+        assert win[np.argmax(np.abs(img[win]))] == kk
+        assert win[np.argmax(np.abs(ref[win]))] == kk
 
 
 def test_invalid_geometry_is_flagged(torch, small):
