@@ -49,6 +49,9 @@ struct sar_plan {
     float2 *d_partial = nullptr;
     int *d_err = nullptr;
     double *d_means = nullptr;  // sar_doppler_offsets: mean positions and velocity
+    // tables of the split-transform range compression (when supported)
+    bool rc_split = false;
+    float2 *d_rc_pre = nullptr, *d_rc_twd = nullptr;
     // staging buffers of sar_form_image_host
     void *s_beat = nullptr;
     float *s_waz = nullptr;
@@ -555,7 +558,30 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
         rot[i] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
 
+    // split-transform range compression: input rotations with the window
+    // folded in, and the inter-pass twiddles (FP64, stored FP32)
+    std::vector<float2> rc_pre, rc_twd;
+    pl->rc_split = rc_split_supported(p.n_samples, p.os);
+    if (pl->rc_split) {
+        const int N = p.n_samples, n2 = N / 32, nf = pl->n_fft;
+        auto ang = [&](long long num, long long den) { return pl->sign * 2.0 * kPi * (double)(num % den) / den; };
+        rc_pre.resize((size_t)p.os * N);
+        for (int q = 0; q < p.os; ++q)
+            for (int n = 0; n < N; ++n) {
+                const double w = wr[n], t = ang((long long)n * q, nf);
+                rc_pre[(size_t)q * N + n] = make_float2((float)(w * std::cos(t)), (float)(w * std::sin(t)));
+            }
+        rc_twd.resize((size_t)n2 * 32);
+        for (int j = 0; j < n2; ++j)
+            for (int k1 = 0; k1 < 32; ++k1) {
+                const double t = ang((long long)j * k1, N);
+                rc_twd[(size_t)k1 * n2 + j] = make_float2((float)std::cos(t), (float)std::sin(t));
+            }
+    }
+
     rc = upload(pl, wr, &pl->d_wr);
+    if (!rc && pl->rc_split) rc = upload(pl, rc_pre, &pl->d_rc_pre);
+    if (!rc && pl->rc_split) rc = upload(pl, rc_twd, &pl->d_rc_twd);
     if (!rc) rc = upload(pl, tw, &pl->d_tw);
     if (!rc) rc = upload(pl, rot, &pl->d_rot);
     if (!rc) rc = upload(pl, ht.pix, &pl->d_pix);
@@ -623,6 +649,24 @@ int rc_launch_part(sar_plan *pl, const void *beat, int m0, int M, int M_tot, con
     }
     DeviceGuard dg(pl->device);
     if (!dg.ok) return SAR_ECUDA;
+    if (pl->rc_split && mode != kRcSpectrum) {
+        RcSplitArgs b{};
+        b.beat = a.beat;
+        b.pre = pl->d_rc_pre;
+        b.twd = pl->d_rc_twd;
+        b.rot = pl->d_rot;
+        b.w_az = a.w_az;
+        b.out = a.out;
+        b.scales = a.scales;
+        b.rows = a.rows;
+        b.R = a.R;
+        b.N2 = pl->p.n_samples / 32;
+        b.os = pl->p.os;
+        b.crop_lo = pl->crop_lo;
+        b.crop_hi = pl->crop_hi;
+        b.n_bins = pl->n_bins;
+        return launch_range_compress_split(b, pl->sign, mode, s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
+    }
     return launch_range_compress(a, pl->sign, mode, s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
 }
 

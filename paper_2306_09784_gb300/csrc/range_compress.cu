@@ -425,6 +425,230 @@ __global__ void __launch_bounds__(256, 2) range_compress_persistent(RcArgs a, lo
     }
 }
 
+// ---------------------------------------------------------------------------
+// Split-transform kernel (the common case: N = 32 N2 samples, N2 in {8, 16,
+// 32}, N2 os <= 256).  With bins k = os q + s (q < N, s < os) the
+// zero-padded transform splits into os N-point transforms
+//     S[os q + s] = sum_{n<N} (w_r[n] x[n] W^{n s}) W_N^{n q},  W = exp(SGN j 2 pi / N_fft),
+// so the zero padding costs only the input rotations W^{n s} (a table with
+// the window folded in).  One thread group of N2 threads runs each N-point
+// transform as 32 x N2: a pass of 32-point DFTs over n1 (n = N2 n1 + j for
+// thread j, 32 complex values in registers), the twiddles W_N^{j k1}, one
+// exchange through shared memory inside the warp (XOR-swizzled, no CTA
+// barrier) and a pass of N2-point DFTs.  Thread j then holds X[k1 + 32 k2]
+// for its k1 = j (32 / N2) + i and all k2; only the cropped bins are rotated,
+// scaled and stored.  Complex values are (re, im) float2: additions are single
+// packed FP32 instructions.
+// ---------------------------------------------------------------------------
+constexpr int kSplitThreads = 256;  // threads per CTA
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as a fused multiply-add by -1 (exact, one instruction)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
+// cos(k pi / 16), k = 0..16
+__device__ __forceinline__ constexpr float cos_pi16(int k) {
+    constexpr float t[17] = {1.0f,
+                             0.98078528040323044913f,
+                             0.92387953251128675613f,
+                             0.83146961230254523708f,
+                             0.70710678118654752440f,
+                             0.55557023301960222474f,
+                             0.38268343236508977173f,
+                             0.19509032201612826785f,
+                             0.0f,
+                             -0.19509032201612826785f,
+                             -0.38268343236508977173f,
+                             -0.55557023301960222474f,
+                             -0.70710678118654752440f,
+                             -0.83146961230254523708f,
+                             -0.92387953251128675613f,
+                             -0.98078528040323044913f,
+                             -1.0f};
+    return t[k];
+}
+
+// One radix-2 butterfly of a decimation-in-time stage: a + w b, a - w b with
+// w = exp(SGN j pi E / 16), E in [0, 16).  Quarter turns are swaps.
+template <int SGN, int E>
+__device__ __forceinline__ void bfly(float2 &a, float2 &b) {
+    float2 wb = b;
+    if (E == 8) {
+        wb = SGN > 0 ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x);
+    } else if (E != 0) {
+        constexpr float c = cos_pi16(E);
+        constexpr float sn = (SGN > 0 ? 1.0f : -1.0f) * (E <= 8 ? cos_pi16(8 - E) : cos_pi16(E - 8));
+        wb = make_float2(fmaf(b.x, c, -b.y * sn), fmaf(b.x, sn, b.y * c));
+    }
+    const float2 x = a;
+    a = add2(x, wb);
+    b = sub2(x, wb);
+}
+
+// Stage of span H of an R-point DIT transform (R <= 32): butterflies
+// (s + t, s + t + H) with w = exp(SGN j 2 pi t / (2 H)) = exp(SGN j pi e / 16),
+// e = t * 16 / H.
+template <int R, int SGN, int H, int T = 0>
+__device__ __forceinline__ void stage_t(float2 *v) {
+    if constexpr (T < H) {
+#pragma unroll
+        for (int s = 0; s < R; s += 2 * H) bfly<SGN, T * 16 / H>(v[s + T], v[s + T + H]);
+        stage_t<R, SGN, H, T + 1>(v);
+    }
+}
+
+// In-register R-point DFT (R = 8, 16, 32), natural order in and out:
+//   v[k] <- sum_n v[n] exp(SGN j 2 pi n k / R).
+template <int R, int SGN>
+__device__ __forceinline__ void dft_small(float2 *v) {
+    constexpr int bits = R == 8 ? 3 : R == 16 ? 4 : 5;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int j = bitrev(i, bits);
+        if (i < j) {
+            const float2 t = v[i];
+            v[i] = v[j];
+            v[j] = t;
+        }
+    }
+    stage_t<R, SGN, 1>(v);
+    stage_t<R, SGN, 2>(v);
+    stage_t<R, SGN, 4>(v);
+    if constexpr (R >= 16) stage_t<R, SGN, 8>(v);
+    if constexpr (R >= 32) stage_t<R, SGN, 16>(v);
+}
+
+// Exchange / output region per sub-transform: at least N + N2 float2 (the
+// padded transpose layout needs N + N2 - 1; the outputs use the first N),
+// rounded so that the stride is 16 / os modulo 16 elements: the output stage
+// reads bins k, k + 1, ... from the os regions in turn (k mod os), and that
+// stride puts the 16 lanes of a half-warp on 16 different bank pairs.
+__host__ __device__ constexpr int split_region(int n2, int os) {
+    const int base = 32 * n2 + n2;
+    const int want = os >= 16 ? 1 : 16 / os;
+    return base + (((want - base) % 16) + 16) % 16;
+}
+
+template <int SGN, int MODE, int N2>
+__global__ void __launch_bounds__(kSplitThreads, 2) range_compress_split(RcSplitArgs a, long long n_groups) {
+    constexpr int N = 32 * N2;
+    constexpr int C = 32 / N2;  // pass-2 transforms per thread
+    extern __shared__ __align__(16) float2 xbuf[];  // [sub-transforms of the CTA][REG]
+    __shared__ float row_max[kSplitThreads / 32];
+    const int os = a.os;
+    const int REG = split_region(N2, os);  // float2 per region
+    const int RT = N2 * os;               // threads per row
+    const int RPC = kSplitThreads / RT;   // rows per CTA
+    const int lrow = threadIdx.x / RT;
+    const int rem = threadIdx.x - lrow * RT;
+    const int s = rem / N2;               // sub-transform: bins os q + s
+    const int j = rem - s * N2;           // thread within the sub-transform
+    float2 *xb = xbuf + (threadIdx.x / N2) * REG;   // this sub-transform's region
+    float2 *xrow = xbuf + lrow * os * REG;          // the row's first region
+    const float2 *pre = a.pre + (size_t)s * N + j;  // w_r[n] W^(n s) at n = N2 n1 + j
+    const float2 *twd = a.twd + j;                   // W_N^(j k1) at [k1][j]
+    const int sh_os = 31 - __clz(os);
+
+    for (long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
+        const long long row = g * RPC + lrow;
+        const bool active = row < a.rows;
+        const float2 *x = a.beat + (active ? row : 0) * (long long)N;
+        // L2 prefetch of the row this thread group handles next (one 128-byte
+        // line per thread)
+        {
+            const long long nrow = (g + gridDim.x) * RPC + lrow;
+            if (nrow < a.rows && rem * 16 < N)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a.beat + nrow * (long long)N + rem * 16));
+        }
+        float2 v[32];
+#pragma unroll
+        for (int n1 = 0; n1 < 32; ++n1) {
+            const float2 xv = active ? __ldg(x + N2 * n1 + j) : make_float2(0.f, 0.f);
+            const float2 t = __ldg(pre + N2 * n1);
+            v[n1] = make_float2(fmaf(xv.x, t.x, -xv.y * t.y), fmaf(xv.x, t.y, xv.y * t.x));
+        }
+        dft_small<32, SGN>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < 32; ++k1) {
+            const float2 w = __ldg(twd + k1 * N2);
+            const float2 b = v[k1];
+            v[k1] = make_float2(fmaf(b.x, w.x, -b.y * w.y), fmaf(b.x, w.y, b.y * w.x));
+        }
+        // exchange A[j][k1] -> thread owning k1: element (k1, jj) sits at
+        // k1 N2 + k1 / C + jj.  Writes of one k1 are consecutive; thread j
+        // reads its k1 = j C + i at j (C N2 + 1) + i N2 + jj, a stride of
+        // C N2 + 1 = 33 elements between threads (16 bank pairs per half-warp).
+        // Every address is a per-thread base plus a constant.
+#pragma unroll
+        for (int k1 = 0; k1 < 32; ++k1) xb[k1 * N2 + k1 / C + j] = v[k1];
+        __syncwarp();
+        {
+            const float2 *rd = xb + j * (C * N2 + 1);
+#pragma unroll
+            for (int i = 0; i < C; ++i)
+#pragma unroll
+                for (int jj = 0; jj < N2; ++jj) v[i * N2 + jj] = rd[i * N2 + jj];
+        }
+#pragma unroll
+        for (int i = 0; i < C; ++i) dft_small<N2, SGN>(v + i * N2);
+        // X[q] with q = k1 + 32 k2 (k1 = j C + i) back into the region, by q
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < C; ++i)
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) xb[j * C + i + 32 * k2] = v[i * N2 + k2];
+        __syncthreads();
+
+        // cropped bins k in [crop_lo, crop_hi], RT consecutive bins per step
+        // across the row's threads: X = sub-transform k mod os at q = k / os,
+        // times the per-bin rotation and w_sar
+        const float g_az = (a.w_az != nullptr && active) ? __ldg(a.w_az + row / a.R) : 1.f;
+        if (MODE == kRcProfileF32) {
+            if (active) {
+                float2 *out = reinterpret_cast<float2 *>(a.out) + row * (long long)a.n_bins - a.crop_lo;
+                for (int k = a.crop_lo + rem; k <= a.crop_hi; k += RT) {
+                    const float2 b = xrow[(k & (os - 1)) * REG + (k >> sh_os)];
+                    const float2 r = __ldg(a.rot + (k - a.crop_lo));
+                    out[k] = make_float2(g_az * fmaf(b.x, r.x, -b.y * r.y), g_az * fmaf(b.x, r.y, b.y * r.x));
+                }
+            }
+            __syncthreads();  // the regions are rewritten by the next row
+        } else {
+            float mx = 0.f;
+            if (active) {
+                for (int k = a.crop_lo + rem; k <= a.crop_hi; k += RT) {
+                    const float2 b = xrow[(k & (os - 1)) * REG + (k >> sh_os)];
+                    const float2 r = __ldg(a.rot + (k - a.crop_lo));
+                    mx = fmaxf(mx, fmaxf(fabsf(g_az * fmaf(b.x, r.x, -b.y * r.y)),
+                                         fabsf(g_az * fmaf(b.x, r.y, b.y * r.x))));
+                }
+            }
+            // row maximum: within the warp's lanes of the row, then across the
+            // row's warps (RT >= 32) through shared memory
+            const int span = RT < 32 ? RT : 32;
+            for (int o = span >> 1; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (RT > 32) {
+                if ((threadIdx.x & 31) == 0) row_max[threadIdx.x >> 5] = mx;
+                __syncthreads();
+                const int w0 = (lrow * RT) >> 5;
+                for (int w = 0; w < (RT >> 5); ++w) mx = fmaxf(mx, row_max[w0 + w]);
+            }
+            if (active) {
+                const float scale = mx > 0.f ? mx * (1.0f / 16384.0f) : 1.0f;
+                const float inv = g_az / scale;
+                if (rem == 0) a.scales[row] = scale;
+                __half2 *out = reinterpret_cast<__half2 *>(a.out) + row * (long long)a.n_bins - a.crop_lo;
+                for (int k = a.crop_lo + rem; k <= a.crop_hi; k += RT) {
+                    const float2 b = xrow[(k & (os - 1)) * REG + (k >> sh_os)];
+                    const float2 r = __ldg(a.rot + (k - a.crop_lo));
+                    out[k] = __floats2half2_rn(inv * fmaf(b.x, r.x, -b.y * r.y), inv * fmaf(b.x, r.y, b.y * r.x));
+                }
+            }
+            __syncthreads();  // the regions and row_max are rewritten by the next row
+        }
+    }
+}
+
 template <int SGN, int MODE>
 cudaError_t launch_rc(const RcArgs &a, cudaStream_t s) {
     const int n = a.n_fft;
@@ -474,7 +698,41 @@ cudaError_t launch_rc(const RcArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int SGN, int MODE>
+cudaError_t launch_split(const RcSplitArgs &a, cudaStream_t s) {
+    auto kern = a.N2 == 32   ? range_compress_split<SGN, MODE, 32>
+                : a.N2 == 16 ? range_compress_split<SGN, MODE, 16>
+                             : range_compress_split<SGN, MODE, 8>;
+    const int rpc = kSplitThreads / (a.N2 * a.os);
+    const long long n_groups = (a.rows + rpc - 1) / rpc;
+    if (n_groups == 0) return cudaSuccess;
+    // one region per sub-transform of the CTA (66 KB at N2 = 32)
+    const size_t smem = (size_t)(kSplitThreads / a.N2) * split_region(a.N2, a.os) * sizeof(float2);
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kSplitThreads, smem) != cudaSuccess || occ < 1)
+        return cudaErrorInvalidConfiguration;
+    const long long grid = std::min<long long>(n_groups, (long long)sms * occ);
+    kern<<<(unsigned)grid, kSplitThreads, smem, s>>>(a, n_groups);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+bool rc_split_supported(int n_samples, int os) {
+    if (os < 1 || os > 16 || (os & (os - 1)) != 0) return false;
+    const int n2 = n_samples / 32;
+    if (n_samples != 32 * n2 || (n2 != 8 && n2 != 16 && n2 != 32)) return false;
+    return n2 * os <= kSplitThreads;
+}
+
+cudaError_t launch_range_compress_split(const RcSplitArgs &a, int sign, int mode, cudaStream_t s) {
+    if (mode == kRcSpectrum || !rc_split_supported(32 * a.N2, a.os)) return cudaErrorInvalidValue;
+    if (sign > 0) return mode == kRcProfileF16 ? launch_split<1, kRcProfileF16>(a, s) : launch_split<1, kRcProfileF32>(a, s);
+    return mode == kRcProfileF16 ? launch_split<-1, kRcProfileF16>(a, s) : launch_split<-1, kRcProfileF32>(a, s);
+}
 
 cudaError_t launch_range_compress(const RcArgs &a, int sign, int mode, cudaStream_t s) {
     if (sign > 0) {

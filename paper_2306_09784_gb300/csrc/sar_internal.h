@@ -44,6 +44,23 @@ struct RcArgs {
 
 cudaError_t launch_range_compress(const RcArgs &a, int sign, int mode, cudaStream_t s);
 
+// Split-transform range compression (N = 32 N2 samples, N2 in {8, 16, 32},
+// N2 os <= 256): tables built by the plan.
+struct RcSplitArgs {
+    const float2 *beat;  // [rows][N]
+    const float2 *pre;   // [os][N]: w_r[n] exp(SGN j 2 pi n s / N_fft), input rotation of sub-transform s
+    const float2 *twd;   // [32][N2]: W_N^(j k1) at [k1][j]
+    const float2 *rot;   // [n_bins]: per-bin rotation of the stored profile
+    const float *w_az;   // [M] or null
+    void *out;           // profile samples
+    float *scales;       // [rows] (FP16 profiles)
+    long long rows;
+    int R, N2, os;
+    int crop_lo, crop_hi, n_bins;
+};
+bool rc_split_supported(int n_samples, int os);
+cudaError_t launch_range_compress_split(const RcSplitArgs &a, int sign, int mode, cudaStream_t s);
+
 // Per-tile data: reference point (x, y), radius rho (max distance of the
 // tile's points from the reference), number of valid points, and two
 // plan-dependent constants of the expansion loop: o_allow, the largest Rx

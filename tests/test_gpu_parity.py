@@ -98,6 +98,60 @@ def test_profile_vs_oracle(torch, small, precision):
         assert err < 2e-3, err
 
 
+SPLIT_CASES = [
+    # (N, os, precision, sign, M, R, crop (None = full valid range))
+    (1024, 4, 1, 1, 9, 4, (1207, 1833)),     # the precision frame's shape, odd crop start
+    (1024, 4, 0, -1, 5, 3, (0, 4094)),       # conjugate convention, whole valid range
+    (1024, 2, 1, 1, 11, 2, (301, 1500)),     # two sub-transforms per row, four rows per CTA
+    (1024, 8, 0, 1, 3, 4, (2000, 6100)),     # eight sub-transforms per row (256 threads)
+    (1024, 1, 1, 1, 10, 3, (5, 1000)),       # no zero padding
+    (512, 4, 0, 1, 7, 3, (512, 1101)),       # the full frame's shape, ragged rows
+    (512, 16, 1, 1, 4, 2, (17, 8190)),       # sixteen sub-transforms of 16 threads
+    (256, 8, 1, -1, 13, 1, (33, 2046)),      # 8-thread sub-transforms
+    (256, 16, 0, 1, 6, 2, (3, 4093)),
+]
+
+
+@pytest.mark.parametrize("case", SPLIT_CASES, ids=lambda c: f"N{c[0]}-os{c[1]}-p{c[2]}-s{c[3]}")
+def test_profile_split_kernel_vs_oracle(torch, case):
+    """The split-transform range compression (N = 256, 512, 1024, os sub-
+    transforms of N points) against the oracle: stored profile =
+    w_sar[m] rot[k] S[m][r][k] over the crop, FP32 or FP16 with a
+    per-(chirp, Rx) scale."""
+    N, os_factor, precision, sign, M, R, crop = case
+    radar = synth.Radar(n_samples=N, n_rx=R, os=os_factor)
+    rng = np.random.Generator(np.random.PCG64(N * os_factor + M))
+    beat = (rng.standard_normal((M, R, N)) + 1j * rng.standard_normal((M, R, N))).astype(np.complex64)
+    w_az = rng.uniform(0.2, 1.0, M)
+    grid = synth.Grid(0.0, 2.0, 0.05, 0.05, 4, 4)
+    import paper_2306_09784_gb300 as sar
+    plan = sar.Plan.from_radar(radar, max_pulses=M, grid=grid, precision=precision, crop=crop,
+                               phase_sign=sign)
+    b = torch.from_numpy(beat).cuda()
+    w = torch.from_numpy(w_az.astype(np.float32)).cuda()
+    prof = plan.range_compress(b, w).cpu().numpy()
+    lo, hi = crop
+    nb = hi - lo + 1
+    S = oracle.range_compress(beat, oracle.window(1, N), os_factor, sign=sign)
+    ref = w_az.astype(np.float32).astype(np.float64)[:, None, None] * \
+        rotation(radar, crop, sign)[None, None, :] * S[:, :, lo:hi + 1]
+    if precision == 0:
+        got = prof.view(np.complex64).reshape(M, R, nb)
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err < 2e-6, err
+    else:
+        pad = (M * R * 4 + 255) // 256 * 256
+        scale = prof[:M * R * 4].view(np.float32).reshape(M, R)
+        h = prof[pad:pad + M * R * nb * 4].view(np.float16).reshape(M, R, nb, 2).astype(np.float64)
+        got = (h[..., 0] + 1j * h[..., 1]) * scale[..., None]
+        rowmax = np.abs(ref).max(axis=-1)
+        err = (np.abs(got - ref) / rowmax[..., None]).max()
+        assert err < 2e-3, err
+        # the scale maps each row's largest component to 2^14
+        comp = np.maximum(np.abs(h[..., 0]), np.abs(h[..., 1])).max(axis=-1)
+        assert np.all(np.abs(comp - 16384.0) <= 16.0), comp
+
+
 def test_profile_from_8_byte_aligned_beat(torch, small):
     """A beat cube that starts 8 bytes past a 16-byte boundary takes the
     8-byte staging copies and gives the same profiles bit for bit."""
