@@ -383,6 +383,12 @@ def bench_batched(dev, stream, reps=5, n_req=64, seed=5):
                          img_plain=torch.zeros(plan.n_pixels, dtype=torch.complex64, device=dev),
                          img_batch=torch.zeros(plan.n_pixels, dtype=torch.complex64, device=dev)))
     upd = sum(r["wl"].grid.nx * r["wl"].grid.ny * r["wl"].n_pulses * r["wl"].radar.n_rx for r in reqs)
+    # tuned launch shapes for both arms: each plan's own (used by the
+    # per-request launches; remembered per size bucket, so similar requests
+    # share a tuning), then the batch's per-class shapes
+    for r in reqs:
+        r["plan"].range_compress(r["beat"], r["w"], out=r["prof"], stream=stream)
+        r["plan"].autotune(r["prof"], r["wl"].n_pulses, r["qt"], r["qr"], r["img_plain"], stream=stream)
 
     def plain():
         for r in reqs:
@@ -395,6 +401,9 @@ def bench_batched(dev, stream, reps=5, n_req=64, seed=5):
         batch.add(r["plan"], r["prof"], r["wl"].n_pulses, r["qt"], r["qr"], r["img_batch"])
     with torch.cuda.stream(stream):
         batch.commit(stream)
+        for r in reqs:
+            r["plan"].range_compress(r["beat"], r["w"], out=r["prof"], stream=stream)
+        classes = batch.autotune(stream)
     stream.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
@@ -427,9 +436,12 @@ def bench_batched(dev, stream, reps=5, n_req=64, seed=5):
             "plain_ms": t_plain * 1e3, "batched_ms": t_batch * 1e3,
             "speedup": t_plain / t_batch, "batched_gupdates_per_s": upd / t_batch / 1e9,
             "max_rel_l2_batched_vs_plain": max(errs), "work_units": units, "ctas": ctas,
+            "classes": classes,
             "config": "64 requests, 128-1024 chirps x 512 samples, 128^2-768^2 px at 2.5 cm, "
-                      "1-4 Rx, FP16 profiles; batched = same range compressions + one persistent "
-                      "backprojection launch, replayed as one CUDA graph"}
+                      "1-4 Rx, FP16 profiles; plain = per-request range compression + "
+                      "backprojection launches with each plan's autotuned shape; batched = same "
+                      "range compressions + one persistent backprojection launch over all "
+                      "classes (autotuned per class) + one fix-up, replayed as one CUDA graph"}
 
 
 def bench_served(dev, duration_s=3.0, seed=7, n_saturate=40):
@@ -579,20 +591,27 @@ def run_ours(args):
     pipes = sar.alu_peaks()
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
     upd = P * M * R
+    # Inputs larger than L2: identical copies of the beat cube, used in turn,
+    # so that every step reads a cube the other copies (and the steps'
+    # profiles) have evicted from L2.  (A write flush between steps would
+    # leave ~129 MB of dirty lines whose write-back then competes with the
+    # range compression's reads.)
+    n_cubes = max(3, -(-3 * L2_BYTES // (beat.numel() * beat.element_size())))
+    beats = [beat] + [beat.clone() for _ in range(n_cubes - 1)]
+    cube_bytes = beat.numel() * beat.element_size()
 
-    def step(ev=None):
+    def step(ev=None, k=0):
         if ev is not None:
             ev[0].record(stream)
-        plan.range_compress(beat, w, out=prof, stream=stream)
+        plan.range_compress(beats[k % n_cubes], w, out=prof, stream=stream)
         if ev is not None:
             ev[1].record(stream)
         plan.backproject(prof, M, qt, qr, image=image, stream=stream)
         if ev is not None:
             ev[2].record(stream)
 
-    for _ in range(args.warmup):
-        flush.zero_()
-        step()
+    for k in range(args.warmup):
+        step(k=k)
     torch.cuda.synchronize(dev)
     if plan.check_errors() != 0:
         raise RuntimeError("kernel reported invalid geometry")
@@ -605,8 +624,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     sampler.start()
     for k in range(args.steps):
-        flush.zero_()  # L2 flush between timed steps (outside the timed events)
-        step(events[k])
+        step(events[k], k=args.warmup + k)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
     if ws > 1:
@@ -653,7 +671,9 @@ def run_ours(args):
                                "1000 point scatterers",
                    "global_batch": ws, "parallelism": f"replicas{ws}",
                    "profile_storage": args.precision,
-                   "l2": "flushed between timed steps (2 x 129 MB write)",
+                   "l2": f"inputs larger than L2: {n_cubes} identical copies of the "
+                         f"{cube_bytes / 1e6:.0f} MB beat cube read in turn "
+                         f"({n_cubes * cube_bytes / 1e6:.0f} MB > 129 MB L2)",
                    "pulse_count": "one pulse = one (chirp, Rx) range profile",
                    "bp_launch_shape": shape},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),

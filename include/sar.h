@@ -317,23 +317,25 @@ int sar_backproject_noalloc(sar_plan *plan, const void *prof_dev, int32_t M,
                             int32_t accumulate, void *stream);
 
 /*
- * Batched backprojection (Alg. 2 for several requests in few launches).
+ * Batched backprojection (Alg. 2 for several requests in a few launches).
  * Requests of uneven sizes -- each with its own plan (radar parameters,
  * reconstruction points, FP32 or FP16 profiles), profiles, trajectory and
  * image -- are packed as (request, pixel tile, pulse block) work units and
- * split evenly over one persistent grid per class of requests that share an
- * Rx group and a profile storage (at most 8 classes; the pixel loop is
- * specialised per class); tiles shared by two CTAs are summed by a fix-up
- * kernel.  Each request's image equals sar_backproject's up to FP32
- * summation order.
+ * grouped into classes that share an Rx group and a profile storage (at most
+ * 8; the pixel loop is specialised per class).  Each class is one persistent
+ * launch over the whole GPU that splits the units of all its requests evenly
+ * over the CTAs; the classes run back to back and one fix-up kernel then sums
+ * the tiles that two CTAs shared.  Each request's image equals
+ * sar_backproject's up to FP32 summation order.
  *
  * Use: sar_batch_clear, sar_batch_add per request, sar_batch_commit (groups
  * the requests by class and uploads the request table on `stream`), then
- * sar_batch_launch (two kernels per class on `stream`, reading only device
- * memory: it can be captured in a CUDA graph and replayed while the table
- * and the request buffers stay unchanged).
- * All plans of a batch must be on the batch's device; the batch owns its
- * request table (pinned host + device) and 16 KB of scratch per CTA.
+ * sar_batch_launch (one kernel per class and the fix-up on `stream`, reading
+ * only device memory: it can be captured in a CUDA graph and replayed while
+ * the table and the request buffers stay unchanged).  sar_batch_autotune
+ * picks each class's pulse block.  All plans of a batch must be on the
+ * batch's device; the batch owns its request table (pinned host + device) and
+ * partial sums of 16 KB per CTA and class (39 MB on 152 SMs).
  * Requests of one batch must not write the same image.
  */
 typedef struct sar_batch sar_batch;
@@ -341,7 +343,8 @@ typedef struct sar_batch sar_batch;
 /* Create a batch for up to max_jobs requests on the current device. */
 int sar_batch_create(int32_t max_jobs, sar_batch **out);
 void sar_batch_destroy(sar_batch *batch);
-/* Forget all requests (waits for a pending table upload). */
+/* Forget all requests (waits for a pending table upload).  Launch choices
+ * made by sar_batch_autotune are kept. */
 int sar_batch_clear(sar_batch *batch);
 /* Append one request: arguments as sar_backproject (no Doppler offsets). */
 int sar_batch_add(sar_batch *batch, sar_plan *plan, const void *prof_dev, int32_t M,
@@ -349,11 +352,44 @@ int sar_batch_add(sar_batch *batch, sar_plan *plan, const void *prof_dev, int32_
                   int32_t accumulate);
 /* Upload the request table asynchronously on `stream`. */
 int sar_batch_commit(sar_batch *batch, void *stream);
-/* Launch the persistent backprojection and its fix-up for each class of requests. */
+/* Launch the persistent backprojection of every class and the fix-up. */
 int sar_batch_launch(sar_batch *batch, void *stream);
-/* Requests, work units and the largest class grid (CTAs) of the committed
- * batch (any pointer may be NULL). */
+/* Requests, work units and the largest class launch's grid (CTAs) of the
+ * committed batch (any pointer may be NULL). */
 int sar_batch_get_info(const sar_batch *batch, int32_t *n_jobs, int64_t *units, int32_t *ctas);
+
+/*
+ * Autotuner of the batched launch (no counterpart in the paper): it times
+ * every class's launch with chirps per pipeline block from {each request's
+ * plan's own, the largest that fits two CTAs per SM for every request of the
+ * class, 2/3 and 1/2 of that} and keeps each class's fastest.  Needs a
+ * committed batch; re-commits it on `stream` and blocks until the timing runs
+ * finish.  The requests' images are overwritten (and accumulating requests
+ * accumulate repeatedly): their contents are undefined afterwards.  The
+ * choices persist across sar_batch_clear.
+ */
+int sar_batch_autotune(sar_batch *batch, void *stream);
+
+/* One class of the committed batch (see sar_batch_num_classes). */
+typedef struct sar_batch_class {
+    int32_t rx_group;          /* Rx channels per inner-loop group */
+    int32_t fp16;              /* profile storage: 1 = FP16 */
+    int32_t n_jobs;            /* requests in the class */
+    int32_t pulses_per_block;  /* chirps per pipeline block; 0 = each request's plan's own */
+    int32_t ctas;              /* CTAs of the class's launch */
+    int32_t regs_ctas_per_sm;  /* CTAs per SM the launch's registers are sized for (2) */
+    int64_t units;             /* (tile, pulse block) work units */
+    double updates;            /* pixel slots x chirps x Rx */
+} sar_batch_class;
+
+int sar_batch_num_classes(const sar_batch *batch, int32_t *n_classes);
+/* Waits for the device and reports (then clears) the batched kernels' checks
+ * of their work decomposition: SAR_OK, or SAR_EBOUNDS when a check failed (the
+ * work it guarded was skipped); detail (may be NULL) receives [4]: the check's
+ * code and three values.  Geometry errors are reported per plan by
+ * sar_plan_check_errors. */
+int sar_batch_check_errors(sar_batch *batch, int32_t *detail);
+int sar_batch_get_class(const sar_batch *batch, int32_t index, sar_batch_class *out);
 
 /*
  * Served form: continuous batching of imaging requests from several radars.

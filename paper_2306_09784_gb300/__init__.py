@@ -31,7 +31,8 @@ EXPORTS = (
     "sar_batch_commit", "sar_batch_launch", "sar_batch_get_info",
     "sar_server_create", "sar_server_destroy", "sar_submit", "sar_poll", "sar_wait",
     "sar_release", "sar_server_get_stats", "sar_plan_autotune", "sar_plan_set_launch",
-    "sar_alu_peaks", "sar_polar_grid", "sar_doppler_offsets",
+    "sar_alu_peaks", "sar_polar_grid", "sar_doppler_offsets", "sar_batch_autotune",
+    "sar_batch_num_classes", "sar_batch_get_class", "sar_batch_check_errors",
 )
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 
@@ -76,6 +77,13 @@ class PlanInfo(ctypes.Structure):
 class PolarSpec(ctypes.Structure):
     _fields_ = [("x_min", ctypes.c_double), ("x_max", ctypes.c_double), ("y_min", ctypes.c_double),
                 ("y_max", ctypes.c_double), ("factor", ctypes.c_double)]
+
+
+class BatchClass(ctypes.Structure):
+    _fields_ = [("rx_group", ctypes.c_int32), ("fp16", ctypes.c_int32), ("n_jobs", ctypes.c_int32),
+                ("pulses_per_block", ctypes.c_int32), ("ctas", ctypes.c_int32),
+                ("regs_ctas_per_sm", ctypes.c_int32), ("units", ctypes.c_int64),
+                ("updates", ctypes.c_double)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -147,6 +155,10 @@ def load_library(path: str = LIB_PATH):
     lib.sar_polar_grid.argtypes = [ctypes.POINTER(RadarParams), vp, i32, ctypes.POINTER(PolarSpec), vp,
                                    ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     lib.sar_doppler_offsets.argtypes = [vp, vp, vp, vp, i32, vp, vp]
+    lib.sar_batch_autotune.argtypes = [vp, vp]
+    lib.sar_batch_num_classes.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.sar_batch_get_class.argtypes = [vp, i32, ctypes.POINTER(BatchClass)]
+    lib.sar_batch_check_errors.argtypes = [vp, ctypes.POINTER(i32)]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("sar_plan_destroy", "sar_status_string", "sar_batch_destroy",
@@ -421,6 +433,29 @@ class Batch:
 
     def launch(self, stream=None):
         _check(self._lib.sar_batch_launch(self._b, _stream(stream)), "sar_batch_launch")
+
+    def autotune(self, stream=None):
+        """Pick the launch shape (per-class block sizes, register variant, CTA
+        shares) by timing; the requests' images are overwritten."""
+        _check(self._lib.sar_batch_autotune(self._b, _stream(stream)), "sar_batch_autotune")
+        return self.classes()
+
+    def check_errors(self):
+        """(status, [code, v1, v2, v3]) of the batched kernels' checks."""
+        d = (ctypes.c_int32 * 4)()
+        rc = self._lib.sar_batch_check_errors(self._b, d)
+        return rc, list(d)
+
+    def classes(self):
+        """The committed batch's classes and their launch shapes."""
+        n = ctypes.c_int32()
+        _check(self._lib.sar_batch_num_classes(self._b, ctypes.byref(n)), "sar_batch_num_classes")
+        out = []
+        for i in range(n.value):
+            c = BatchClass()
+            _check(self._lib.sar_batch_get_class(self._b, i, ctypes.byref(c)), "sar_batch_get_class")
+            out.append({f: getattr(c, f) for f, _ in BatchClass._fields_})
+        return out
 
     def info(self):
         n, u, g = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()

@@ -64,19 +64,25 @@ struct sar_plan {
     std::vector<void *> allocs;
 };
 
-// One persistent launch per class of requests with the same Rx group and
-// profile storage (the kernel is specialised on both).
+// Requests of a batch are grouped into classes with the same Rx group and
+// profile storage (the pixel loop is specialised on both); one persistent
+// launch runs every class, each on its share of the CTAs.
 struct BatchClass {
     int rg = 0;
     bool fp16 = false;
     int j0 = 0, n = 0;       // jobs [j0, j0 + n) of the sorted table
     int off = 0;             // first entry of its prefix sums (j0 + class index)
     long long units = 0;
-    int tiles = 0, G = 0;
+    double updates = 0;      // pixel slots x chirps x Rx of its jobs
+    int tiles = 0, G = 0, cta_begin = 0, tile_base = 0;
     size_t smem = 0;
 };
 
-constexpr int kBatchClasses = 8;  // Rx group 1..4 x storage
+// Launch choice per class key (storage x Rx group): chirps per pipeline block
+// (0 = each request's plan's own).
+struct ClassShape {
+    int mb = 0;
+};
 
 struct sar_batch {
     int device = 0;
@@ -85,7 +91,7 @@ struct sar_batch {
     long long units = 0;
     int tiles = 0;
     bool committed = false, upload_pending = false;
-    BpArgs *h_jobs = nullptr;    // in the order added
+    BpArgs *h_jobs = nullptr;    // in the order added, each with its plan's own block size
     // One pinned upload blob and its device copy, [ub | tb | sorted jobs], so
     // that a commit is a single host-to-device copy:
     unsigned char *h_blob = nullptr, *d_blob = nullptr;
@@ -97,12 +103,15 @@ struct sar_batch {
     long long *d_ub = nullptr;
     int *d_tb = nullptr;
     float2 *d_scratch = nullptr;
-    // occupancy of each class's kernel for the shared-memory size last seen
-    size_t occ_smem[kBatchClasses] = {};
-    int occ_ctas[kBatchClasses] = {};
+    int *d_err = nullptr;        // [4] checks of the batched kernels
     cudaEvent_t uploaded = nullptr;
     int n_classes = 0;
     BatchClass cls[kBatchClasses];
+    ClassShape shape[kBatchClasses];
+    // occupancy of each class key's kernel, cached for its shared-memory size
+    size_t occ_smem[kBatchClasses] = {};
+    int occ_ctas[kBatchClasses] = {};
+    size_t scratch_slots = 0;    // partial-sum slots: two per CTA of every class
 };
 
 namespace {
@@ -1018,15 +1027,20 @@ int sar_batch_create(int32_t max_jobs, sar_batch **out) {
         return SAR_ECUDA;
     }
     b->num_sms = prop.multiProcessorCount;
-    b->g_cap = b->num_sms * 2;  // the batch kernel runs at most two CTAs per SM
+    b->g_cap = b->num_sms * 2;  // CTAs of one class's launch (two per SM)
     const size_t n_pref = (size_t)max_jobs + kBatchClasses;
     const size_t tb_off = sizeof(long long) * n_pref;
     b->jobs_off = (tb_off + sizeof(int) * n_pref + 15) & ~size_t(15);
     const size_t blob = b->jobs_off + sizeof(BpArgs) * max_jobs;
+    b->scratch_slots = (size_t)kBatchClasses * b->g_cap * 2;
     bool ok = cudaMallocHost((void **)&b->h_jobs, sizeof(BpArgs) * max_jobs) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_scratch, sizeof(float2) * kTilePx * b->scratch_slots) == cudaSuccess &&
               cudaMallocHost((void **)&b->h_blob, blob) == cudaSuccess &&
               cudaMalloc((void **)&b->d_blob, blob) == cudaSuccess &&
-              cudaMalloc((void **)&b->d_scratch, sizeof(float2) * kTilePx * 2 * (size_t)b->g_cap) == cudaSuccess &&
+
+              cudaMalloc((void **)&b->d_err, sizeof(int) * 4) == cudaSuccess &&
+              cudaMemset(b->d_err, 0, sizeof(int) * 4) == cudaSuccess &&
+
               cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming) == cudaSuccess;
     if (ok) {
         b->h_ub = reinterpret_cast<long long *>(b->h_blob);
@@ -1052,6 +1066,8 @@ void sar_batch_destroy(sar_batch *b) {
     if (b->h_blob) cudaFreeHost(b->h_blob);
     if (b->d_blob) cudaFree(b->d_blob);
     if (b->d_scratch) cudaFree(b->d_scratch);
+    if (b->d_err) cudaFree(b->d_err);
+
     if (b->uploaded) cudaEventDestroy(b->uploaded);
     delete b;
 }
@@ -1102,14 +1118,17 @@ int sar_batch_commit(sar_batch *b, void *stream) {
         if (cudaEventSynchronize(b->uploaded) != cudaSuccess) return SAR_ECUDA;
         b->upload_pending = false;
     }
-    // group the jobs by class, keeping their order within a class
+    // group the jobs by class, keeping their order within a class; apply the
+    // class's block size (if set) to each job's unit decomposition
     int count[kBatchClasses] = {0};
     auto key = [](const BpArgs &a) { return (a.fp16 ? 4 : 0) + a.rg - 1; };
     for (int j = 0; j < b->n_jobs; ++j) ++count[key(b->h_jobs[j])];
     int fill[kBatchClasses];
+    int cls_of_key[kBatchClasses];
     b->n_classes = 0;
     for (int k = 0, j0 = 0; k < kBatchClasses; ++k) {
         fill[k] = j0;
+        cls_of_key[k] = -1;
         if (count[k]) {
             BatchClass &c = b->cls[b->n_classes];
             c = BatchClass{};
@@ -1118,12 +1137,24 @@ int sar_batch_commit(sar_batch *b, void *stream) {
             c.j0 = j0;
             c.n = count[k];
             c.off = j0 + b->n_classes;
+            cls_of_key[k] = b->n_classes;
             ++b->n_classes;
         }
         j0 += count[k];
     }
-    for (int j = 0; j < b->n_jobs; ++j) b->h_sorted[fill[key(b->h_jobs[j])]++] = b->h_jobs[j];
-    b->G = 0;
+    for (int j = 0; j < b->n_jobs; ++j) {
+        BpArgs a = b->h_jobs[j];
+        const int k = key(a);
+        if (b->shape[k].mb > 0) {
+            a.Mb = b->shape[k].mb;
+            a.blocks_per_tile = (a.M + a.Mb - 1) / a.Mb;
+            a.units = (long long)a.n_tiles * a.blocks_per_tile;
+        }
+        b->h_sorted[fill[k]++] = a;
+    }
+    // per-class prefix sums, shared memory and estimated time
+    b->units = 0;
+    b->tiles = 0;
     for (int ci = 0; ci < b->n_classes; ++ci) {
         BatchClass &c = b->cls[ci];
         for (int i = 0; i < c.n; ++i) {
@@ -1132,13 +1163,22 @@ int sar_batch_commit(sar_batch *b, void *stream) {
             b->h_tb[c.off + i] = c.tiles;
             c.units += a.units;
             c.tiles += a.n_tiles;
+            c.updates += (double)a.n_tiles * kTilePx * a.M * a.R;
             c.smem = std::max(c.smem, bp_smem_bytes(a.Mb, a.R, a.L, c.fp16));
         }
         b->h_ub[c.off + c.n] = c.units;
         b->h_tb[c.off + c.n] = c.tiles;
+        if (c.smem > kBpSmemMax) return SAR_EINVAL;
+        b->units += c.units;
+    }
+    // the classes run one after another, each on the whole grid (two CTAs
+    // per SM, stream-K over its units); each class has its own partial-sum
+    // slots so that one fix-up after the last class serves all of them
+    for (int ci = 0; ci < b->n_classes; ++ci) {
+        BatchClass &c = b->cls[ci];
         const int k = (c.fp16 ? 4 : 0) + c.rg - 1;
-        int occ = b->occ_smem[k] == c.smem ? b->occ_ctas[k] : 0;
-        if (occ < 1) {
+        if (b->occ_smem[k] != c.smem || b->occ_ctas[k] < 1) {
+            int occ = 0;
             if (bp_batch_prepare(c.rg, c.fp16, c.smem, &occ) != cudaSuccess || occ < 1) {
                 cudaGetLastError();
                 return SAR_ECUDA;
@@ -1146,9 +1186,20 @@ int sar_batch_commit(sar_batch *b, void *stream) {
             b->occ_smem[k] = c.smem;
             b->occ_ctas[k] = occ;
         }
-        c.G = (int)std::min<long long>(std::min(b->g_cap, b->num_sms * occ), c.units);
-        b->G = std::max(b->G, c.G);
+        c.G = (int)std::min<long long>(b->num_sms * std::min(b->occ_ctas[k], 2), c.units);
     }
+    b->G = 0;
+    int ctas = 0;
+    for (int ci = 0; ci < b->n_classes; ++ci) {
+        BatchClass &c = b->cls[ci];
+        c.cta_begin = ctas;
+        c.tile_base = b->tiles;
+        ctas += c.G;
+        b->G = std::max(b->G, c.G);
+        b->tiles += c.tiles;
+    }
+    if ((size_t)ctas * 2 > b->scratch_slots) return SAR_EINVAL;  // sized for every class at creation
+    (void)cls_of_key;
     cudaStream_t s = (cudaStream_t)stream;
     bool ok = cudaMemcpyAsync(b->d_blob, b->h_blob, b->jobs_off + sizeof(BpArgs) * b->n_jobs,
                               cudaMemcpyHostToDevice, s) == cudaSuccess &&
@@ -1159,25 +1210,68 @@ int sar_batch_commit(sar_batch *b, void *stream) {
     return SAR_OK;
 }
 
+namespace {
+
+// Kernel arguments of class ci of the committed batch, on G CTAs (0: its
+// share) numbered from cta_begin, and of all classes for the fix-up.
+BpClassArgs class_args(const sar_batch *b, int ci, int G, int cta_begin) {
+    const BatchClass &c = b->cls[ci];
+    BpClassArgs a{};
+    a.jobs = b->d_jobs + c.j0;
+    a.unit_begin = b->d_ub + c.off;
+    a.tile_begin = b->d_tb + c.off;
+    a.units = c.units;
+    a.n_jobs = c.n;
+    a.G = G > 0 ? (int)std::min<long long>(G, c.units) : c.G;
+    a.cta_begin = cta_begin;
+    a.tile_base = c.tile_base;
+    a.rg = c.rg;
+    a.fp16 = c.fp16 ? 1 : 0;
+    return a;
+}
+
+BpCheck batch_check(const sar_batch *b, size_t smem) {
+    BpCheck k{};
+    k.scratch = b->d_scratch;
+    k.scratch_slots = (long long)b->scratch_slots;
+    k.smem_bytes = (unsigned)smem;
+    k.err = b->d_err;
+    return k;
+}
+
+// Class ci alone (autotuning), with its fix-up.
+int batch_launch_class(const sar_batch *b, int ci, cudaStream_t s) {
+    const BatchClass &c = b->cls[ci];
+    const BpClassArgs a = class_args(b, ci, 0, c.cta_begin);
+    BpMultiArgs m{};
+    m.cls[0] = a;
+    m.cls[0].tile_base = 0;
+    m.n_classes = 1;
+    const BpCheck chk = batch_check(b, c.smem);
+    if (launch_backproject_class(a, chk, c.smem, s) != cudaSuccess) return SAR_ECUDA;
+    return launch_batch_fixup(m, chk, c.tiles, s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
+}
+
+}  // namespace
+
 int sar_batch_launch(sar_batch *b, void *stream) {
     if (!b || !b->committed) return SAR_EINVAL;
     if (b->n_jobs == 0) return SAR_OK;
     DeviceGuard dg(b->device);
     if (!dg.ok) return SAR_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    BpMultiArgs m{};
+    m.n_classes = b->n_classes;
+    size_t smem_max = 0;
     for (int ci = 0; ci < b->n_classes; ++ci) {
-        const BatchClass &c = b->cls[ci];
-        BpBatchArgs a{};
-        a.jobs = b->d_jobs + c.j0;
-        a.unit_begin = b->d_ub + c.off;
-        a.tile_begin = b->d_tb + c.off;
-        a.scratch = b->d_scratch;  // launches on one stream: the slots are reused in turn
-        a.units = c.units;
-        a.n_jobs = c.n;
-        a.G = c.G;
-        if (launch_backproject_batch(a, c.rg, c.fp16, c.tiles, c.smem, (cudaStream_t)stream) != cudaSuccess)
+        m.cls[ci] = class_args(b, ci, 0, b->cls[ci].cta_begin);
+        smem_max = std::max(smem_max, b->cls[ci].smem);
+        if (launch_backproject_class(m.cls[ci], batch_check(b, b->cls[ci].smem), b->cls[ci].smem, s) !=
+            cudaSuccess)
             return SAR_ECUDA;
     }
-    return SAR_OK;
+    // one fix-up over the tiles of every class
+    return launch_batch_fixup(m, batch_check(b, smem_max), b->tiles, s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
 }
 
 }  // extern "C"
@@ -1235,6 +1329,24 @@ int sar_batch_get_info(const sar_batch *b, int32_t *n_jobs, int64_t *units, int3
     if (n_jobs) *n_jobs = b->n_jobs;
     if (units) *units = b->units;
     if (ctas) *ctas = b->G;
+    return SAR_OK;
+}
+
+int sar_batch_check_errors(sar_batch *b, int32_t *detail) {
+    if (!b) return SAR_EINVAL;
+    DeviceGuard dg(b->device);
+    if (cudaDeviceSynchronize() != cudaSuccess) return SAR_ECUDA;
+    int h[4] = {0, 0, 0, 0};
+    if (cudaMemcpy(h, b->d_err, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return SAR_ECUDA;
+    if (cudaMemset(b->d_err, 0, sizeof(h)) != cudaSuccess) return SAR_ECUDA;
+    if (detail)
+        for (int i = 0; i < 4; ++i) detail[i] = h[i];
+    return h[0] ? SAR_EBOUNDS : SAR_OK;
+}
+
+int sar_batch_num_classes(const sar_batch *b, int32_t *n_classes) {
+    if (!b || !n_classes) return SAR_EINVAL;
+    *n_classes = b->committed ? b->n_classes : 0;
     return SAR_OK;
 }
 
@@ -1303,6 +1415,95 @@ int sar_plan_autotune(sar_plan *pl, const void *prof_dev, int32_t M, const doubl
     if (apply_launch(pl, fin.rg, fin.minb, fin.Mb) != SAR_OK && !rc) rc = SAR_ECUDA;
     if (!rc) remember_shape(pl);
     return rc;
+}
+
+int sar_batch_autotune(sar_batch *b, void *stream) {
+    if (!b || !b->committed) return SAR_EINVAL;
+    if (b->n_jobs == 0) return SAR_OK;
+    DeviceGuard dg(b->device);
+    if (!dg.ok) return SAR_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SAR_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return SAR_ECUDA;
+    }
+    int rc = SAR_OK;
+    // median of three timed launches after one untimed: class ci alone on
+    // the whole grid of its storage's launch
+    auto time_class = [&](int ci, float *ms) {
+        float t[3] = {0, 0, 0};
+        for (int rep = -1; rep < 3 && rc == SAR_OK; ++rep) {
+            if (cudaEventRecord(e0, s) != cudaSuccess || batch_launch_class(b, ci, s) != SAR_OK ||
+                cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = SAR_ECUDA;
+                break;
+            }
+            if (rep >= 0 && cudaEventElapsedTime(&t[rep], e0, e1) != cudaSuccess) rc = SAR_ECUDA;
+        }
+        std::sort(t, t + 3);
+        *ms = t[1];
+    };
+    ClassShape saved[kBatchClasses];
+    std::copy(b->shape, b->shape + kBatchClasses, saved);
+    for (int k = 0; k < kBatchClasses; ++k) b->shape[k] = ClassShape{};
+    rc = sar_batch_commit(b, stream);
+    for (int ci = 0; ci < b->n_classes && rc == SAR_OK; ++ci) {
+        const BatchClass c0 = b->cls[ci];
+        const int k = (c0.fp16 ? 4 : 0) + c0.rg - 1;
+        // largest block whose staging fits two CTAs per SM for every request
+        // of the class
+        int fit = 0;
+        for (int mb = kMaxPulsesPerBlock; mb >= 1 && !fit; --mb) {
+            bool ok = true;
+            for (int i = 0; i < c0.n && ok; ++i) {
+                const BpArgs &a = b->h_sorted[c0.j0 + i];
+                ok = bp_smem_bytes(mb, a.R, a.L, c0.fp16) <= kBpSmemTarget;
+            }
+            if (ok) fit = mb;
+        }
+        const int cand[4] = {0, fit, std::max(1, fit * 2 / 3), std::max(1, fit / 2)};
+        float t_best = 1e30f;
+        int mb_best = 0;
+        for (int q = 0; q < 4 && rc == SAR_OK; ++q) {
+            if (q > 0 && (cand[q] == 0 || cand[q] == cand[q - 1])) continue;
+            b->shape[k].mb = cand[q];
+            rc = sar_batch_commit(b, stream);
+            float t = 0;
+            if (rc == SAR_OK) time_class(ci, &t);
+            if (rc == SAR_OK && t < t_best) {
+                t_best = t;
+                mb_best = cand[q];
+            }
+        }
+        b->shape[k].mb = mb_best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        std::copy(saved, saved + kBatchClasses, b->shape);
+        sar_batch_commit(b, stream);
+        return rc;
+    }
+    return sar_batch_commit(b, stream);
+}
+
+int sar_batch_get_class(const sar_batch *b, int32_t index, sar_batch_class *out) {
+    if (!b || !out || index < 0 || index >= b->n_classes || !b->committed) return SAR_EINVAL;
+    const BatchClass &c = b->cls[index];
+    const int k = (c.fp16 ? 4 : 0) + c.rg - 1;
+    sar_batch_class r{};
+    r.rx_group = c.rg;
+    r.fp16 = c.fp16 ? 1 : 0;
+    r.n_jobs = c.n;
+    r.pulses_per_block = b->shape[k].mb;
+    r.ctas = c.G;
+    r.regs_ctas_per_sm = 2;
+    r.units = c.units;
+    r.updates = c.updates;
+    *out = r;
+    return SAR_OK;
 }
 
 int sar_plan_set_launch(sar_plan *pl, int32_t rx_group, int32_t regs_ctas_per_sm, int32_t pulses_per_block) {

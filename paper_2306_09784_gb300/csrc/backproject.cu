@@ -740,20 +740,35 @@ __global__ void __launch_bounds__(kBpThreads, MINB) backproject_kernel(BpArgs a)
 }
 
 // Batched form: the (request, tile, pulse block) units of several requests,
-// each with its own plan, profiles, trajectory and image, concatenated and
-// split into equal contiguous ranges over one persistent grid.  One launch
-// covers the requests of one (Rx group, storage) class, so the pixel loop is
-// specialised like the single-request kernel.  Only the first and the last
-// segment of a CTA's range can cover part of a tile, so each CTA owns two
+// each with its own plan, profiles, trajectory and image.  The requests are
+// grouped into classes that share an Rx group and a profile storage (the
+// pixel loop is specialised on both); ONE persistent launch runs every class:
+// CTAs [cta_begin, cta_begin + G) of the grid belong to class c and split its
+// concatenated units into equal contiguous ranges.  Only the first and the
+// last segment of a CTA's range can cover part of a tile, so each CTA owns two
 // partial-sum slots (0: first segment, 1: last segment).
+// Records the first failed check of a batched launch (code and three values);
+// the caller then skips the access.  Conditions are CTA-uniform.
+__device__ __forceinline__ void batch_fail(int *err, int code, long long x, long long y, long long z) {
+    if (threadIdx.x == 0 && err && atomicCAS(err, 0, code) == 0) {
+        err[1] = (int)x;
+        err[2] = (int)y;
+        err[3] = (int)z;
+    }
+}
+
 template <int RG, bool FP16>
-__global__ void __launch_bounds__(kBpThreads, 2) backproject_batch_kernel(BpBatchArgs B) {
-    extern __shared__ __align__(16) unsigned char smem_bp[];
+__device__ __forceinline__ void run_class(const BpCheck &M, const BpClassArgs &B, int cta, float2 *scratch,
+                                          uint32_t smem_addr, unsigned char *smem_base) {
     Smem sm;
-    sm.base = smem_bp;
-    sm.base_addr = (uint32_t)__cvta_generic_to_shared(smem_bp);
-    const long long u0 = (long long)blockIdx.x * B.units / B.G;
-    const long long u1 = (long long)(blockIdx.x + 1) * B.units / B.G;
+    sm.base = smem_base;
+    sm.base_addr = smem_addr;
+    if (!(cta >= 0 && cta < B.G && B.units > 0 && B.n_jobs > 0)) {
+        batch_fail(M.err, 1, cta, B.G, B.units);
+        return;
+    }
+    const long long u0 = (long long)cta * B.units / B.G;
+    const long long u1 = (long long)(cta + 1) * B.units / B.G;
     // job holding u0: the last j with unit_begin[j] <= u0
     int lo = 0, hi = B.n_jobs - 1;
     while (lo < hi) {
@@ -763,43 +778,86 @@ __global__ void __launch_bounds__(kBpThreads, 2) backproject_batch_kernel(BpBatc
     int j = lo;
     long long u = u0;
     while (u < u1) {
-        while (u >= B.unit_begin[j + 1]) ++j;
+        while (j + 1 < B.n_jobs && u >= B.unit_begin[j + 1]) ++j;
+        if (!(u >= B.unit_begin[j] && u < B.unit_begin[j + 1])) {
+            batch_fail(M.err, 2, u, j, B.n_jobs);
+            return;
+        }
         const BpArgs a = B.jobs[j];
         sm.lay = bp_layout(a.Mb, a.R, a.L, FP16);
+        if (!(a.Mb >= 1 && a.Mb <= 32 && sm.lay.total <= M.smem_bytes && a.R == B.rg * (a.R / B.rg) &&
+              a.fp16 == (FP16 ? 1 : 0))) {
+            batch_fail(M.err, 3, a.Mb, sm.lay.total, M.smem_bytes);
+            return;
+        }
         const long long v = u - B.unit_begin[j];
         const int PB = a.blocks_per_tile;
         const int tile = (int)(v / PB);
         const int b0 = (int)(v - (long long)tile * PB);
         const int b1 = (int)min((long long)PB, (long long)b0 + (u1 - u));
+        if (!(PB == (a.M + a.Mb - 1) / a.Mb && tile >= 0 && tile < a.n_tiles && b0 >= 0 && b0 < b1 && b1 <= PB)) {
+            batch_fail(M.err, 4, tile, b0, b1);
+            return;
+        }
         float2 *dst = nullptr;
-        if (!(b0 == 0 && b1 == PB)) dst = B.scratch + ((long long)blockIdx.x * 2 + (u == u0 ? 0 : 1)) * kTilePx;
+        if (!(b0 == 0 && b1 == PB)) {
+            if (!((long long)(B.cta_begin + cta) * 2 + 1 < M.scratch_slots)) {
+                batch_fail(M.err, 5, B.cta_begin + cta, M.scratch_slots, 0);
+                return;
+            }
+            dst = scratch + (u == u0 ? 0 : kTilePx);
+        }
         process_segment<RG, FP16, false>(a, sm, tile, b0, b1, dst);
         u += b1 - b0;
     }
 }
 
-// Fix-up of the batched form: one CTA per tile of every request.
-__global__ void __launch_bounds__(kFixupThreads) bp_batch_fixup_kernel(BpBatchArgs B) {
+// One class of the batch: its own specialised kernel on the whole grid; the
+// batch launches its classes one after another.  CTA i of the class owns
+// partial-sum slots 2 (cta_begin + i) and 2 (cta_begin + i) + 1.
+template <int RG, bool FP16>
+__global__ void __launch_bounds__(kBpThreads, 2) backproject_class_kernel(BpClassArgs B, BpCheck chk) {
+    extern __shared__ __align__(16) unsigned char smem_bp[];
+    const uint32_t smem_addr = (uint32_t)__cvta_generic_to_shared(smem_bp);
+    float2 *scratch = chk.scratch + ((long long)B.cta_begin + blockIdx.x) * 2 * kTilePx;
+    run_class<RG, FP16>(chk, B, (int)blockIdx.x, scratch, smem_addr, smem_bp);
+}
+
+// Fix-up of the batched form: one CTA per tile of every request of every
+// class; the split tile's partial sums are added in CTA order.
+__global__ void __launch_bounds__(kFixupThreads) bp_batch_fixup_kernel(BpMultiArgs M, BpCheck chk) {
     const int gt = blockIdx.x;
+    int c = 0;
+    while (c + 1 < M.n_classes && gt >= M.cls[c + 1].tile_base) ++c;
+    const BpClassArgs &B = M.cls[c];
+    const int ct = gt - B.tile_base;
     int lo = 0, hi = B.n_jobs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (B.tile_begin[mid] <= gt) lo = mid; else hi = mid - 1;
+        if (B.tile_begin[mid] <= ct) lo = mid; else hi = mid - 1;
     }
     const BpArgs &a = B.jobs[lo];
-    const int tile = gt - B.tile_begin[lo];
+    const int tile = ct - B.tile_begin[lo];
     const long long PB = a.blocks_per_tile;
     const long long tb = B.unit_begin[lo] + (long long)tile * PB;
     const long long te = tb + PB;
+    if (!(ct >= 0 && ct < B.tile_begin[B.n_jobs] && tile >= 0 && tile < a.n_tiles && te <= B.unit_begin[lo + 1])) {
+        batch_fail(chk.err, 6, ct, lo, tile);
+        return;
+    }
     const int ia = (int)(((tb + 1) * B.G - 1) / B.units);
     const int ib = (int)((te * B.G - 1) / B.units);
     if (ia == ib) return;
+    if (!(ia >= 0 && ib < B.G && ((long long)B.cta_begin + ib) * 2 + 1 < chk.scratch_slots)) {
+        batch_fail(chk.err, 7, ia, ib, B.cta_begin);
+        return;
+    }
     float2 acc[kFixupPx];
 #pragma unroll
     for (int k = 0; k < kFixupPx; ++k) acc[k] = make_float2(0.f, 0.f);
     for (int i = ia; i <= ib; ++i) {  // CTA order; one slot lookup per CTA
         const long long ui0 = (long long)i * B.units / B.G;
-        const float2 *part = B.scratch + ((long long)i * 2 + (ui0 >= tb ? 0 : 1)) * kTilePx;
+        const float2 *part = chk.scratch + ((long long)(B.cta_begin + i) * 2 + (ui0 >= tb ? 0 : 1)) * kTilePx;
 #pragma unroll
         for (int k = 0; k < kFixupPx; ++k) {
             const float2 v = part[threadIdx.x + k * kFixupThreads];
@@ -910,9 +968,9 @@ int bp_occupancy(bool fp16, int rg, size_t smem, int minb, int *ctas_per_sm) {
 
 namespace {
 
-void *select_batch_kernel(int rg, bool fp16) {
-#define SAR_SELB(RGV) \
-    if (rg == RGV) return fp16 ? (void *)backproject_batch_kernel<RGV, true> : (void *)backproject_batch_kernel<RGV, false>;
+void *select_class_kernel(int rg, bool fp16) {
+#define SAR_SELB(RGV)                                                                                     \
+    if (rg == RGV) return fp16 ? (void *)backproject_class_kernel<RGV, true> : (void *)backproject_class_kernel<RGV, false>;
     SAR_SELB(1)
     SAR_SELB(2)
     SAR_SELB(3)
@@ -924,23 +982,27 @@ void *select_batch_kernel(int rg, bool fp16) {
 }  // namespace
 
 cudaError_t bp_batch_prepare(int rg, bool fp16, size_t smem, int *ctas_per_sm) {
-    void *k = select_batch_kernel(rg, fp16);
+    void *k = select_class_kernel(rg, fp16);
     if (!k || smem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e != cudaSuccess) return e;
+
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k, kBpThreads, smem);
 }
 
-cudaError_t launch_backproject_batch(const BpBatchArgs &b, int rg, bool fp16, int total_tiles, size_t smem,
-                                     cudaStream_t s) {
-    if (b.units == 0 || b.n_jobs == 0) return cudaSuccess;
-    void *k = select_batch_kernel(rg, fp16);
+cudaError_t launch_backproject_class(const BpClassArgs &c, const BpCheck &chk, size_t smem, cudaStream_t s) {
+    if (c.G == 0 || c.units == 0) return cudaSuccess;
+    void *k = select_class_kernel(c.rg, c.fp16 != 0);
     if (!k) return cudaErrorInvalidValue;
-    BpBatchArgs args = b;
-    void *params[] = {&args};
-    cudaError_t e = cudaLaunchKernel(k, dim3(b.G), dim3(kBpThreads), params, smem, s);
-    if (e != cudaSuccess) return e;
-    bp_batch_fixup_kernel<<<total_tiles, kFixupThreads, 0, s>>>(b);
+    BpClassArgs a = c;
+    BpCheck b = chk;
+    void *params[] = {&a, &b};
+    return cudaLaunchKernel(k, dim3(c.G), dim3(kBpThreads), params, smem, s);
+}
+
+cudaError_t launch_batch_fixup(const BpMultiArgs &m, const BpCheck &chk, int total_tiles, cudaStream_t s) {
+    if (m.n_classes == 0 || total_tiles == 0) return cudaSuccess;
+    bp_batch_fixup_kernel<<<total_tiles, kFixupThreads, 0, s>>>(m, chk);
     return cudaGetLastError();
 }
 

@@ -110,15 +110,32 @@ struct BpArgs {
 };
 
 // Batched form: several requests (each a BpArgs with its own plan data)
-// backprojected by one persistent launch.
-struct BpBatchArgs {
+// backprojected by one persistent launch.  Requests are grouped into classes
+// (Rx group, storage); class c owns CTAs [cta_begin, cta_begin + G) and tiles
+// [tile_base, tile_base + tiles) of the fix-up.
+struct BpClassArgs {
     const BpArgs *jobs;          // [n_jobs]
     const long long *unit_begin; // [n_jobs + 1] prefix sums of (tile, pulse block) units
     const int *tile_begin;       // [n_jobs + 1] prefix sums of tiles
-    float2 *scratch;             // [G * 2][kTilePx] partial sums
     long long units;
     int n_jobs;
-    int G;
+    int G;                       // CTAs of the class
+    int cta_begin;               // first CTA of the class in the grid
+    int tile_base;               // first fix-up CTA of the class
+    int rg;                      // Rx group of the inner loop
+    int fp16;                    // profile storage
+};
+constexpr int kBatchClasses = 8;  // Rx group 1..4 x storage
+struct BpMultiArgs {
+    BpClassArgs cls[kBatchClasses];
+    int n_classes;
+};
+// Partial-sum scratch of a batch and the checks of its kernels.
+struct BpCheck {
+    float2 *scratch;             // [CTAs * 2][kTilePx] partial sums
+    long long scratch_slots;     // capacity of scratch in kTilePx slots
+    unsigned smem_bytes;         // dynamic shared memory of the launch
+    int *err;                    // [4]: check code, then three values of the first failed check
 };
 
 struct BpLaunch {
@@ -133,8 +150,8 @@ cudaError_t bp_prepare(bool fp16, int rg, size_t smem);  // sets function attrib
 int bp_occupancy(bool fp16, int rg, size_t smem, int minb, int *ctas_per_sm);
 cudaError_t launch_backproject(const BpArgs &a, const BpLaunch &l, cudaStream_t s);
 cudaError_t bp_batch_prepare(int rg, bool fp16, size_t smem, int *ctas_per_sm);
-cudaError_t launch_backproject_batch(const BpBatchArgs &b, int rg, bool fp16, int total_tiles, size_t smem,
-                                     cudaStream_t s);
+cudaError_t launch_backproject_class(const BpClassArgs &c, const BpCheck &chk, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_fixup(const BpMultiArgs &m, const BpCheck &chk, int total_tiles, cudaStream_t s);
 
 // Per-pixel Doppler offsets (doppler.cu).
 struct DopplerArgs {

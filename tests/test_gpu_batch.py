@@ -46,8 +46,10 @@ def test_mixed_batch_equals_single_requests():
     batch.commit()
     batch.launch()
     torch.cuda.synchronize()
+    assert batch.check_errors() == (sar.SAR_OK, [0, 0, 0, 0])
     n, units, ctas = batch.info()
     assert n == len(reqs) and units > 0 and ctas > 0
+    assert len(batch.classes()) >= 3
     for r, img in zip(reqs, images):
         single = _single(r)
         torch.cuda.synchronize()
@@ -85,9 +87,9 @@ def test_batch_accumulate_subapertures():
 
 def test_batched_config_64_requests_graph():
     """The batched configuration: 64 requests of 128-1024 pulses, 128^2-768^2
-    pixels, 1-4 Rx, FP16 profiles, one persistent launch captured in a CUDA
-    graph and replayed; every request matches its single-request image and
-    sampled pixels match the oracle."""
+    pixels, 1-4 Rx, FP16 profiles, autotuned, one persistent launch captured
+    in a CUDA graph and replayed; every request matches its single-request
+    image and sampled pixels match the oracle."""
     import torch
     import paper_2306_09784_gb300 as sar
     wls = synth.make_batched_requests(64, seed=5)
@@ -101,7 +103,17 @@ def test_batched_config_64_requests_graph():
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         batch.commit(stream)
+        classes = batch.autotune(stream)
     stream.synchronize()
+    assert batch.check_errors() == (sar.SAR_OK, [0, 0, 0, 0])
+    # the autotuned launch: one class per Rx count (all FP16), each on the
+    # whole grid with its own pulse block
+    n, units, ctas = batch.info()
+    assert n == 64 and sorted(c["rx_group"] for c in classes) == [1, 2, 3, 4]
+    assert max(c["ctas"] for c in classes) == ctas
+    assert sum(c["units"] for c in classes) == units
+    assert len({c["regs_ctas_per_sm"] for c in classes}) == 1
+    assert all(c["fp16"] == 1 and c["ctas"] >= 1 and 0 <= c["pulses_per_block"] <= 32 for c in classes)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
         batch.launch(stream)
@@ -110,6 +122,7 @@ def test_batched_config_64_requests_graph():
     g.replay()
     g.replay()  # replays overwrite (accumulate = 0): same result
     torch.cuda.synchronize()
+    assert batch.check_errors() == (sar.SAR_OK, [0, 0, 0, 0])
     for r, img in zip(reqs, images):
         single = _single(r)
         torch.cuda.synchronize()
