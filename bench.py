@@ -398,17 +398,16 @@ def bench_batched(dev, stream, reps=5, n_req=64, seed=5):
 
     batch = sar.Batch(len(reqs))
     for r in reqs:
-        batch.add(r["plan"], r["prof"], r["wl"].n_pulses, r["qt"], r["qr"], r["img_batch"])
+        r["prof_batch"] = torch.empty_like(r["prof"])
+        batch.add_frame(r["plan"], r["beat"], r["w"], r["prof_batch"], r["wl"].n_pulses, r["qt"], r["qr"],
+                        r["img_batch"])
     with torch.cuda.stream(stream):
         batch.commit(stream)
-        for r in reqs:
-            r["plan"].range_compress(r["beat"], r["w"], out=r["prof"], stream=stream)
+        batch.launch(stream)  # range compressions into the profiles the autotuner reads
         classes = batch.autotune(stream)
     stream.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
-        for r in reqs:
-            r["plan"].range_compress(r["beat"], r["w"], out=r["prof"], stream=stream)
         batch.launch(stream)
 
     def timed(fn):
@@ -439,9 +438,10 @@ def bench_batched(dev, stream, reps=5, n_req=64, seed=5):
             "classes": classes,
             "config": "64 requests, 128-1024 chirps x 512 samples, 128^2-768^2 px at 2.5 cm, "
                       "1-4 Rx, FP16 profiles; plain = per-request range compression + "
-                      "backprojection launches with each plan's autotuned shape; batched = same "
-                      "range compressions + one persistent backprojection launch over all "
-                      "classes (autotuned per class) + one fix-up, replayed as one CUDA graph"}
+                      "backprojection launches with each plan's autotuned shape; batched = the same "
+                      "frames: packed range compression (one launch per transform shape) + one "
+                      "persistent backprojection launch per class (autotuned pulse block) + one "
+                      "fix-up, replayed as one CUDA graph"}
 
 
 def bench_served(dev, duration_s=3.0, seed=7, n_saturate=40):

@@ -350,9 +350,23 @@ int sar_batch_clear(sar_batch *batch);
 int sar_batch_add(sar_batch *batch, sar_plan *plan, const void *prof_dev, int32_t M,
                   const double *q_tx_dev, const double *q_rx_dev, void *image_dev,
                   int32_t accumulate);
+/*
+ * Append one frame: its range compression (as sar_range_compress of beat_dev
+ * and w_az_dev into prof_dev) and its backprojection (as sar_batch_add of
+ * prof_dev).  sar_batch_launch then range-compresses the batch's frames
+ * first: frames of the same transform shape (samples, zero padding,
+ * convention, storage) in one packed launch of the split-transform kernel
+ * when it supports the shape, each frame in its own launch otherwise.
+ *  beat_dev  complex64 [M][R][N] (8-byte aligned);  w_az_dev float [M] or NULL;
+ *  prof_dev  sar_profile_bytes(M) bytes (256-byte aligned), written by the launch.
+ */
+int sar_batch_add_frame(sar_batch *batch, sar_plan *plan, const void *beat_dev, const float *w_az_dev,
+                        void *prof_dev, int32_t M, const double *q_tx_dev, const double *q_rx_dev,
+                        void *image_dev, int32_t accumulate);
 /* Upload the request table asynchronously on `stream`. */
 int sar_batch_commit(sar_batch *batch, void *stream);
-/* Launch the persistent backprojection of every class and the fix-up. */
+/* Launch the range compressions of the frames added with sar_batch_add_frame,
+ * then the persistent backprojection of every class and the fix-up. */
 int sar_batch_launch(sar_batch *batch, void *stream);
 /* Requests, work units and the largest class launch's grid (CTAs) of the
  * committed batch (any pointer may be NULL). */

@@ -32,7 +32,7 @@ EXPORTS = (
     "sar_server_create", "sar_server_destroy", "sar_submit", "sar_poll", "sar_wait",
     "sar_release", "sar_server_get_stats", "sar_plan_autotune", "sar_plan_set_launch",
     "sar_alu_peaks", "sar_polar_grid", "sar_doppler_offsets", "sar_batch_autotune",
-    "sar_batch_num_classes", "sar_batch_get_class", "sar_batch_check_errors",
+    "sar_batch_num_classes", "sar_batch_get_class", "sar_batch_check_errors", "sar_batch_add_frame",
 )
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 
@@ -159,6 +159,7 @@ def load_library(path: str = LIB_PATH):
     lib.sar_batch_num_classes.argtypes = [vp, ctypes.POINTER(i32)]
     lib.sar_batch_get_class.argtypes = [vp, i32, ctypes.POINTER(BatchClass)]
     lib.sar_batch_check_errors.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.sar_batch_add_frame.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, i32]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("sar_plan_destroy", "sar_status_string", "sar_batch_destroy",
@@ -427,6 +428,21 @@ class Batch:
         _check(self._lib.sar_batch_add(self._b, plan.handle, _ptr(prof), M, _ptr(q_tx), _ptr(q_rx),
                                        _ptr(image), 1 if accumulate else 0), "sar_batch_add")
         self._keep.append((plan, prof, q_tx, q_rx, image))
+
+    def add_frame(self, plan: "Plan", beat, w_az, prof, M: int, q_tx, q_rx, image,
+                  accumulate: bool = False):
+        """A frame whose range compression (beat -> prof) runs in the batch's
+        packed launch before its backprojection."""
+        import torch
+        _require_cuda(beat, "beat", torch.complex64)
+        _require_cuda(w_az, "w_az", torch.float32)
+        _require_cuda(q_tx, "q_tx", torch.float64)
+        _require_cuda(q_rx, "q_rx", torch.float64)
+        _require_cuda(image, "image", torch.complex64)
+        _check(self._lib.sar_batch_add_frame(self._b, plan.handle, _ptr(beat), _ptr(w_az), _ptr(prof), M,
+                                             _ptr(q_tx), _ptr(q_rx), _ptr(image),
+                                             1 if accumulate else 0), "sar_batch_add_frame")
+        self._keep.append((plan, beat, w_az, prof, q_tx, q_rx, image))
 
     def commit(self, stream=None):
         _check(self._lib.sar_batch_commit(self._b, _stream(stream)), "sar_batch_commit")

@@ -112,6 +112,31 @@ struct sar_batch {
     size_t occ_smem[kBatchClasses] = {};
     int occ_ctas[kBatchClasses] = {};
     size_t scratch_slots = 0;    // partial-sum slots: two per CTA of every class
+    // range compressions of frames added with sar_batch_add_frame: jobs of the
+    // split kernel grouped into one launch per (N, os, convention, storage)
+    // class; frames whose shape needs the general kernel get their own launch
+    struct RcJob {
+        RcSplitArgs a;
+        int sign = 1, mode = 0;
+        bool split = false;
+        sar_plan *plan = nullptr;
+        const void *beat = nullptr;
+        const float *w_az = nullptr;
+        void *prof = nullptr;
+        int M = 0;
+    };
+    std::vector<RcJob> rc;
+    struct RcClass {
+        RcSplitArgs a;           // shape (N2, os) of its jobs
+        int sign = 1, mode = 0;
+        int j0 = 0, n = 0, off = 0;
+        long long groups = 0;
+    };
+    RcClass rcc[kBatchClasses];
+    int n_rcc = 0;
+    size_t rc_off = 0, rc_jobs_off = 0;  // blob offsets of the group prefix sums and the jobs
+    long long *h_rgb = nullptr, *d_rgb = nullptr;
+    RcSplitArgs *h_rjobs = nullptr, *d_rjobs = nullptr;
 };
 
 namespace {
@@ -629,10 +654,28 @@ size_t profile_bytes(const sar_plan *pl, int M) {
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 
-// Range compression of pulses [m0, m0 + M) of a profile buffer laid out for
-// M_tot pulses; `beat` and `w_az` point at pulse m0.
-int rc_launch_part(sar_plan *pl, const void *beat, int m0, int M, int M_tot, const float *w_az, void *out,
-                   int mode, cudaStream_t s) {
+// Split-kernel job from the general kernel's arguments and the plan's tables.
+void split_args(const sar_plan *pl, const RcArgs &a, RcSplitArgs *b) {
+    b->beat = a.beat;
+    b->pre = pl->d_rc_pre;
+    b->twd = pl->d_rc_twd;
+    b->rot = pl->d_rot;
+    b->w_az = a.w_az;
+    b->out = a.out;
+    b->scales = a.scales;
+    b->rows = a.rows;
+    b->R = a.R;
+    b->N2 = pl->p.n_samples / 32;
+    b->os = pl->p.os;
+    b->crop_lo = pl->crop_lo;
+    b->crop_hi = pl->crop_hi;
+    b->n_bins = pl->n_bins;
+}
+
+// General-kernel arguments of range compression of pulses [m0, m0 + M) of a
+// profile buffer laid out for M_tot pulses; `beat` and `w_az` point at pulse m0.
+RcArgs rc_args(const sar_plan *pl, const void *beat, int m0, int M, int M_tot, const float *w_az, void *out,
+               int mode) {
     RcArgs a{};
     a.beat = (const float2 *)beat;
     a.w_r = pl->d_wr;
@@ -656,24 +699,19 @@ int rc_launch_part(sar_plan *pl, const void *beat, int m0, int M, int M_tot, con
     } else {
         a.out = (float2 *)out + r0 * pl->n_fft;
     }
+    return a;
+}
+
+// Range compression of pulses [m0, m0 + M) of a profile buffer laid out for
+// M_tot pulses; `beat` and `w_az` point at pulse m0.
+int rc_launch_part(sar_plan *pl, const void *beat, int m0, int M, int M_tot, const float *w_az, void *out,
+                   int mode, cudaStream_t s) {
+    const RcArgs a = rc_args(pl, beat, m0, M, M_tot, w_az, out, mode);
     DeviceGuard dg(pl->device);
     if (!dg.ok) return SAR_ECUDA;
     if (pl->rc_split && mode != kRcSpectrum) {
         RcSplitArgs b{};
-        b.beat = a.beat;
-        b.pre = pl->d_rc_pre;
-        b.twd = pl->d_rc_twd;
-        b.rot = pl->d_rot;
-        b.w_az = a.w_az;
-        b.out = a.out;
-        b.scales = a.scales;
-        b.rows = a.rows;
-        b.R = a.R;
-        b.N2 = pl->p.n_samples / 32;
-        b.os = pl->p.os;
-        b.crop_lo = pl->crop_lo;
-        b.crop_hi = pl->crop_hi;
-        b.n_bins = pl->n_bins;
+        split_args(pl, a, &b);
         return launch_range_compress_split(b, pl->sign, mode, s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
     }
     return launch_range_compress(a, pl->sign, mode, s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
@@ -770,6 +808,15 @@ int bp_launch(sar_plan *pl, const void *prof, int M, const double *q_tx, const d
 namespace sar {
 
 int plan_device(const sar_plan *pl) { return pl->device; }
+
+bool fill_rc_split(const sar_plan *pl, const void *beat, int M, const float *w_az, void *prof, RcSplitArgs *out,
+                   int *sign, int *mode) {
+    if (!pl->rc_split) return false;
+    *mode = pl->fp16 ? kRcProfileF16 : kRcProfileF32;
+    *sign = pl->sign;
+    split_args(pl, rc_args(pl, beat, 0, M, M, w_az, prof, *mode), out);
+    return true;
+}
 
 // Kernel arguments of one backprojection request (no scratch; the batched
 // form supplies its own).
@@ -1031,7 +1078,9 @@ int sar_batch_create(int32_t max_jobs, sar_batch **out) {
     const size_t n_pref = (size_t)max_jobs + kBatchClasses;
     const size_t tb_off = sizeof(long long) * n_pref;
     b->jobs_off = (tb_off + sizeof(int) * n_pref + 15) & ~size_t(15);
-    const size_t blob = b->jobs_off + sizeof(BpArgs) * max_jobs;
+    b->rc_off = (b->jobs_off + sizeof(BpArgs) * max_jobs + 15) & ~size_t(15);
+    b->rc_jobs_off = (b->rc_off + sizeof(long long) * n_pref + 15) & ~size_t(15);
+    const size_t blob = b->rc_jobs_off + sizeof(RcSplitArgs) * max_jobs;
     b->scratch_slots = (size_t)kBatchClasses * b->g_cap * 2;
     bool ok = cudaMallocHost((void **)&b->h_jobs, sizeof(BpArgs) * max_jobs) == cudaSuccess &&
               cudaMalloc((void **)&b->d_scratch, sizeof(float2) * kTilePx * b->scratch_slots) == cudaSuccess &&
@@ -1049,6 +1098,10 @@ int sar_batch_create(int32_t max_jobs, sar_batch **out) {
         b->d_ub = reinterpret_cast<long long *>(b->d_blob);
         b->d_tb = reinterpret_cast<int *>(b->d_blob + tb_off);
         b->d_jobs = reinterpret_cast<BpArgs *>(b->d_blob + b->jobs_off);
+        b->h_rgb = reinterpret_cast<long long *>(b->h_blob + b->rc_off);
+        b->d_rgb = reinterpret_cast<long long *>(b->d_blob + b->rc_off);
+        b->h_rjobs = reinterpret_cast<RcSplitArgs *>(b->h_blob + b->rc_jobs_off);
+        b->d_rjobs = reinterpret_cast<RcSplitArgs *>(b->d_blob + b->rc_jobs_off);
     }
     if (!ok) {
         cudaGetLastError();
@@ -1081,7 +1134,33 @@ int sar_batch_clear(sar_batch *b) {
     b->units = 0;
     b->tiles = 0;
     b->n_classes = 0;
+    b->rc.clear();
+    b->n_rcc = 0;
     b->committed = false;
+    return SAR_OK;
+}
+
+int sar_batch_add_frame(sar_batch *b, sar_plan *plan, const void *beat_dev, const float *w_az_dev, void *prof_dev,
+                        int32_t M, const double *q_tx_dev, const double *q_rx_dev, void *image_dev,
+                        int32_t accumulate) {
+    if (!b || !plan || !beat_dev || !aligned(beat_dev, 8) || (w_az_dev && !aligned(w_az_dev, 4))) return SAR_EINVAL;
+    const int rc = sar_batch_add(b, plan, prof_dev, M, q_tx_dev, q_rx_dev, image_dev, accumulate);
+    if (rc) return rc;
+    try {
+        sar_batch::RcJob j;
+        j.plan = plan;
+        j.beat = beat_dev;
+        j.w_az = w_az_dev;
+        j.prof = prof_dev;
+        j.M = M;
+        j.mode = plan->fp16 ? kRcProfileF16 : kRcProfileF32;
+        j.sign = plan->sign;
+        j.split = fill_rc_split(plan, beat_dev, M, w_az_dev, prof_dev, &j.a, &j.sign, &j.mode);
+        b->rc.push_back(j);
+    } catch (...) {
+        b->n_jobs -= 1;  // undo the backprojection request
+        return SAR_ENOMEM;
+    }
     return SAR_OK;
 }
 
@@ -1199,10 +1278,46 @@ int sar_batch_commit(sar_batch *b, void *stream) {
         b->tiles += c.tiles;
     }
     if ((size_t)ctas * 2 > b->scratch_slots) return SAR_EINVAL;  // sized for every class at creation
+    // range-compression classes: split-kernel jobs of the same shape share a
+    // launch; each job owns ceil(rows / rows per CTA group) row groups
+    b->n_rcc = 0;
+    {
+        int placed = 0;
+        std::vector<char> done(b->rc.size(), 0);
+        for (size_t i = 0; i < b->rc.size(); ++i) {
+            const sar_batch::RcJob &ji = b->rc[i];
+            if (!ji.split || done[i] || b->n_rcc == kBatchClasses) continue;
+            sar_batch::RcClass &c = b->rcc[b->n_rcc];
+            c.a = ji.a;
+            c.sign = ji.sign;
+            c.mode = ji.mode;
+            c.j0 = placed;
+            c.n = 0;
+            c.off = placed + b->n_rcc;
+            c.groups = 0;
+            const int rpc = kSplitThreads / (ji.a.N2 * ji.a.os);
+            for (size_t q = i; q < b->rc.size(); ++q) {
+                const sar_batch::RcJob &jq = b->rc[q];
+                if (!jq.split || done[q] || jq.sign != ji.sign || jq.mode != ji.mode || jq.a.N2 != ji.a.N2 ||
+                    jq.a.os != ji.a.os)
+                    continue;
+                done[q] = 1;
+                b->h_rjobs[placed] = jq.a;
+                b->h_rgb[c.off + c.n] = c.groups;
+                c.groups += (jq.a.rows + rpc - 1) / rpc;
+                ++c.n;
+                ++placed;
+            }
+            b->h_rgb[c.off + c.n] = c.groups;
+            ++b->n_rcc;
+        }
+        for (size_t i = 0; i < b->rc.size(); ++i) b->rc[i].split = b->rc[i].split && done[i];
+    }
     (void)cls_of_key;
     cudaStream_t s = (cudaStream_t)stream;
-    bool ok = cudaMemcpyAsync(b->d_blob, b->h_blob, b->jobs_off + sizeof(BpArgs) * b->n_jobs,
-                              cudaMemcpyHostToDevice, s) == cudaSuccess &&
+    const size_t up = b->rc.empty() ? b->jobs_off + sizeof(BpArgs) * b->n_jobs
+                                    : b->rc_jobs_off + sizeof(RcSplitArgs) * b->rc.size();
+    bool ok = cudaMemcpyAsync(b->d_blob, b->h_blob, up, cudaMemcpyHostToDevice, s) == cudaSuccess &&
               cudaEventRecord(b->uploaded, s) == cudaSuccess;
     if (!ok) return SAR_ECUDA;
     b->upload_pending = true;
@@ -1260,6 +1375,18 @@ int sar_batch_launch(sar_batch *b, void *stream) {
     DeviceGuard dg(b->device);
     if (!dg.ok) return SAR_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    // range compressions of frames added with sar_batch_add_frame: one launch
+    // per class, and the general kernel for the other shapes
+    for (int ci = 0; ci < b->n_rcc; ++ci) {
+        const sar_batch::RcClass &c = b->rcc[ci];
+        const RcSplitBatch tab{b->d_rjobs + c.j0, b->d_rgb + c.off, c.n};
+        if (launch_range_compress_split(c.a, c.sign, c.mode, s, &tab, c.groups) != cudaSuccess) return SAR_ECUDA;
+    }
+    for (const sar_batch::RcJob &j : b->rc)
+        if (!j.split) {
+            const int rc = rc_launch(j.plan, j.beat, j.M, j.w_az, j.prof, j.mode, s);
+            if (rc) return rc;
+        }
     BpMultiArgs m{};
     m.n_classes = b->n_classes;
     size_t smem_max = 0;

@@ -440,7 +440,6 @@ __global__ void __launch_bounds__(256, 2) range_compress_persistent(RcArgs a, lo
 // scaled and stored.  Complex values are (re, im) float2: additions are single
 // packed FP32 instructions.
 // ---------------------------------------------------------------------------
-constexpr int kSplitThreads = 256;  // threads per CTA
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 // a - b as a fused multiply-add by -1 (exact, one instruction)
@@ -529,13 +528,29 @@ __host__ __device__ constexpr int split_region(int n2, int os) {
     return base + (((want - base) % 16) + 16) % 16;
 }
 
+// Job of row group g: the launch's single job, or (batched form) the job of
+// the table whose groups [group_begin[j], group_begin[j + 1]) hold g, with g
+// made local to it.
+__device__ __forceinline__ const RcSplitArgs &split_job(const RcSplitArgs &single, const RcSplitBatch &t,
+                                                        long long &g) {
+    if (t.jobs == nullptr) return single;
+    int lo = 0, hi = t.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.group_begin[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    g -= t.group_begin[lo];
+    return t.jobs[lo];
+}
+
 template <int SGN, int MODE, int N2>
-__global__ void __launch_bounds__(kSplitThreads, 2) range_compress_split(RcSplitArgs a, long long n_groups) {
+__global__ void __launch_bounds__(kSplitThreads, 2) range_compress_split(RcSplitArgs a0, RcSplitBatch tab,
+                                                                         long long n_groups) {
     constexpr int N = 32 * N2;
     constexpr int C = 32 / N2;  // pass-2 transforms per thread
     extern __shared__ __align__(16) float2 xbuf[];  // [sub-transforms of the CTA][REG]
     __shared__ float row_max[kSplitThreads / 32];
-    const int os = a.os;
+    const int os = a0.os;  // the same for every job of a launch
     const int REG = split_region(N2, os);  // float2 per region
     const int RT = N2 * os;               // threads per row
     const int RPC = kSplitThreads / RT;   // rows per CTA
@@ -545,20 +560,24 @@ __global__ void __launch_bounds__(kSplitThreads, 2) range_compress_split(RcSplit
     const int j = rem - s * N2;           // thread within the sub-transform
     float2 *xb = xbuf + (threadIdx.x / N2) * REG;   // this sub-transform's region
     float2 *xrow = xbuf + lrow * os * REG;          // the row's first region
-    const float2 *pre = a.pre + (size_t)s * N + j;  // w_r[n] W^(n s) at n = N2 n1 + j
-    const float2 *twd = a.twd + j;                   // W_N^(j k1) at [k1][j]
     const int sh_os = 31 - __clz(os);
 
     for (long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
-        const long long row = g * RPC + lrow;
+        long long gl = g;
+        const RcSplitArgs &a = split_job(a0, tab, gl);
+        const float2 *pre = a.pre + (size_t)s * N + j;  // w_r[n] W^(n s) at n = N2 n1 + j
+        const float2 *twd = a.twd + j;                   // W_N^(j k1) at [k1][j]
+        const long long row = gl * RPC + lrow;
         const bool active = row < a.rows;
         const float2 *x = a.beat + (active ? row : 0) * (long long)N;
         // L2 prefetch of the row this thread group handles next (one 128-byte
         // line per thread)
-        {
-            const long long nrow = (g + gridDim.x) * RPC + lrow;
-            if (nrow < a.rows && rem * 16 < N)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(a.beat + nrow * (long long)N + rem * 16));
+        if (g + gridDim.x < n_groups) {
+            long long gn = g + gridDim.x;
+            const RcSplitArgs &an = split_job(a0, tab, gn);
+            const long long nrow = gn * RPC + lrow;
+            if (nrow < an.rows && rem * 16 < N)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(an.beat + nrow * (long long)N + rem * 16));
         }
         float2 v[32];
 #pragma unroll
@@ -699,12 +718,12 @@ cudaError_t launch_rc(const RcArgs &a, cudaStream_t s) {
 }
 
 template <int SGN, int MODE>
-cudaError_t launch_split(const RcSplitArgs &a, cudaStream_t s) {
+cudaError_t launch_split(const RcSplitArgs &a, const RcSplitBatch &tab, long long groups, cudaStream_t s) {
     auto kern = a.N2 == 32   ? range_compress_split<SGN, MODE, 32>
                 : a.N2 == 16 ? range_compress_split<SGN, MODE, 16>
                              : range_compress_split<SGN, MODE, 8>;
     const int rpc = kSplitThreads / (a.N2 * a.os);
-    const long long n_groups = (a.rows + rpc - 1) / rpc;
+    const long long n_groups = tab.jobs ? groups : (a.rows + rpc - 1) / rpc;
     if (n_groups == 0) return cudaSuccess;
     // one region per sub-transform of the CTA (66 KB at N2 = 32)
     const size_t smem = (size_t)(kSplitThreads / a.N2) * split_region(a.N2, a.os) * sizeof(float2);
@@ -715,7 +734,7 @@ cudaError_t launch_split(const RcSplitArgs &a, cudaStream_t s) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kSplitThreads, smem) != cudaSuccess || occ < 1)
         return cudaErrorInvalidConfiguration;
     const long long grid = std::min<long long>(n_groups, (long long)sms * occ);
-    kern<<<(unsigned)grid, kSplitThreads, smem, s>>>(a, n_groups);
+    kern<<<(unsigned)grid, kSplitThreads, smem, s>>>(a, tab, n_groups);
     return cudaGetLastError();
 }
 
@@ -728,10 +747,15 @@ bool rc_split_supported(int n_samples, int os) {
     return n2 * os <= kSplitThreads;
 }
 
-cudaError_t launch_range_compress_split(const RcSplitArgs &a, int sign, int mode, cudaStream_t s) {
+cudaError_t launch_range_compress_split(const RcSplitArgs &a, int sign, int mode, cudaStream_t s,
+                                        const RcSplitBatch *tab, long long groups) {
     if (mode == kRcSpectrum || !rc_split_supported(32 * a.N2, a.os)) return cudaErrorInvalidValue;
-    if (sign > 0) return mode == kRcProfileF16 ? launch_split<1, kRcProfileF16>(a, s) : launch_split<1, kRcProfileF32>(a, s);
-    return mode == kRcProfileF16 ? launch_split<-1, kRcProfileF16>(a, s) : launch_split<-1, kRcProfileF32>(a, s);
+    const RcSplitBatch t = tab ? *tab : RcSplitBatch{};
+    if (sign > 0)
+        return mode == kRcProfileF16 ? launch_split<1, kRcProfileF16>(a, t, groups, s)
+                                     : launch_split<1, kRcProfileF32>(a, t, groups, s);
+    return mode == kRcProfileF16 ? launch_split<-1, kRcProfileF16>(a, t, groups, s)
+                                 : launch_split<-1, kRcProfileF32>(a, t, groups, s);
 }
 
 cudaError_t launch_range_compress(const RcArgs &a, int sign, int mode, cudaStream_t s) {

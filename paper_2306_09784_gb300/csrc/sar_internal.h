@@ -45,7 +45,9 @@ struct RcArgs {
 cudaError_t launch_range_compress(const RcArgs &a, int sign, int mode, cudaStream_t s);
 
 // Split-transform range compression (N = 32 N2 samples, N2 in {8, 16, 32},
-// N2 os <= 256): tables built by the plan.
+// N2 os <= 256): tables built by the plan.  CTAs of kSplitThreads threads
+// handle kSplitThreads / (N2 os) rows at a time (a row group).
+constexpr int kSplitThreads = 256;
 struct RcSplitArgs {
     const float2 *beat;  // [rows][N]
     const float2 *pre;   // [os][N]: w_r[n] exp(SGN j 2 pi n s / N_fft), input rotation of sub-transform s
@@ -58,8 +60,22 @@ struct RcSplitArgs {
     int R, N2, os;
     int crop_lo, crop_hi, n_bins;
 };
+// Batched form: several jobs with the same N, os, convention and storage in
+// one launch; job j owns row groups [group_begin[j], group_begin[j + 1]).
+struct RcSplitBatch {
+    const RcSplitArgs *jobs;
+    const long long *group_begin;  // [n_jobs + 1]
+    int n_jobs;
+};
 bool rc_split_supported(int n_samples, int os);
-cudaError_t launch_range_compress_split(const RcSplitArgs &a, int sign, int mode, cudaStream_t s);
+// tab == null: the single job a; otherwise a gives N2 and os of the table's
+// jobs and groups is the table's total row-group count.
+cudaError_t launch_range_compress_split(const RcSplitArgs &a, int sign, int mode, cudaStream_t s,
+                                        const RcSplitBatch *tab = nullptr, long long groups = 0);
+// Fills the split-kernel job of range compression of M chirps on `plan`;
+// false when the plan's shape needs the general kernel.
+bool fill_rc_split(const sar_plan *plan, const void *beat, int M, const float *w_az, void *prof, RcSplitArgs *out,
+                   int *sign, int *mode);
 
 // Per-tile data: reference point (x, y), radius rho (max distance of the
 // tile's points from the reference), number of valid points, and two

@@ -160,3 +160,46 @@ def test_batch_mixes_time_origins():
         ref = oracle_image(wl, r["beat"], r["w_az"], t0=t0 if centre else 0.0)
         tol = TOL_FP32 if r["plan"].params.precision == 0 else 5e-3
         assert rel_l2(got, ref) <= tol
+
+
+def test_batch_frames_range_compressed_in_packed_launches():
+    """sar_batch_add_frame: frames of three transform shapes (two packed
+    split-kernel classes and one shape for the general kernel) are range-
+    compressed inside sar_batch_launch; each frame's profiles equal its own
+    sar_range_compress bit for bit and each image equals its single
+    backprojection."""
+    import torch
+    import paper_2306_09784_gb300 as sar
+    shapes = [(512, 4, 1), (512, 4, 1), (256, 8, 0), (512, 4, 1), (128, 4, 1), (256, 8, 0)]
+    frames = []
+    for i, (N, os_f, prec) in enumerate(shapes):
+        radar = synth.Radar(n_samples=N, n_rx=1 + i % 3, os=os_f)
+        M = 40 + 17 * i
+        rng = np.random.Generator(np.random.PCG64(70 + i))
+        q_tx, q_rx = synth.trajectory(radar, M, jitter=0.01, rng=rng)
+        grid = synth.centred_grid(48 + 16 * i, 40 + 8 * i, 0.03, 2.0)
+        tg = np.stack([rng.uniform(-0.5, 0.5, 4), rng.uniform(2.2, 3.0, 4)], 1)
+        am = rng.standard_normal(4) + 1j * rng.standard_normal(4)
+        wl = synth.Workload(f"f{i}", radar, M, grid, q_tx, q_rx, tg, am, 20.0, i,
+                            synth.crop_for(radar, grid, q_tx, q_rx))
+        r = _prepare(wl, precision=prec)
+        r["b"], r["w"], _, _ = to_dev(wl, r["beat"], r["w_az"])
+        frames.append(r)
+    batch = sar.Batch(len(frames))
+    outs = []
+    for r in frames:
+        # zeroed: FP16 profiles leave the padding after the scale table unwritten
+        prof = torch.zeros_like(r["prof"])
+        r["prof"] = r["plan"].range_compress(r["b"], r["w"], out=torch.zeros_like(r["prof"]))
+        img = torch.zeros(r["plan"].n_pixels, dtype=torch.complex64, device="cuda")
+        batch.add_frame(r["plan"], r["b"], r["w"], prof, r["wl"].n_pulses, r["qt"], r["qr"], img)
+        outs.append((prof, img))
+    batch.commit()
+    batch.launch()
+    torch.cuda.synchronize()
+    assert batch.check_errors() == (sar.SAR_OK, [0, 0, 0, 0])
+    for r, (prof, img) in zip(frames, outs):
+        assert torch.equal(prof, r["prof"]), r["wl"].name
+        single = _single(r)
+        torch.cuda.synchronize()
+        assert rel_l2(img.cpu().numpy(), single.cpu().numpy()) < 1e-5, r["wl"].name
