@@ -444,13 +444,20 @@ def bench_batched(dev, stream, reps=5, n_req=64, seed=5):
                       "fix-up, replayed as one CUDA graph"}
 
 
+SERVED_CONFIGS = [  # (chunk_pulses, quantum_mupdates)
+    (2048, 0), (1024, 0), (512, 0), (256, 0), (2048, 2000), (2048, 1000), (2048, 500)]
+
+
 def bench_served(dev, duration_s=3.0, seed=7, n_saturate=40):
     """Served form: 4 simulated radars (images 256^2..1024^2 at 2.5 cm, 4 Rx,
     512 samples, FP16 profiles) submit frames of 256-2048 chirps at seeded
     Poisson rates of 10-40 Hz to one server (continuous batching, HBM-budget
-    admission).  Reports p50/p99 submit-to-image latency and frames/s, and
-    the saturated throughput against sequential per-frame processing through
-    the host-buffer entry point (same frames, same accuracy check)."""
+    admission).  For each round configuration (chunk of chirps per request,
+    or a work quantum per request) the same seeded arrivals give p50/p99
+    submit-to-image latency and frames/s; the configuration with the lowest
+    p99 is the headline, with its saturated throughput against sequential
+    per-frame processing through the host-buffer entry point (same frames,
+    same accuracy check)."""
     import threading
     import torch
     import paper_2306_09784_gb300 as sar
@@ -475,19 +482,78 @@ def bench_served(dev, duration_s=3.0, seed=7, n_saturate=40):
                            w=torch.from_numpy(synth.azimuth_weights(2048).astype(np.float32)).pin_memory(),
                            qt=torch.from_numpy(q_tx).pin_memory(),
                            qr=torch.from_numpy(np.ascontiguousarray(q_rx)).pin_memory()))
-    srv = sar.Server(hbm_budget=8 << 30, max_inflight=64, queue_capacity=4096, chunk_pulses=2048)
 
-    def submit(rd, M, out):
+    def submit(srv, rd, M, out):
         return srv.submit(rd["plan"], rd["beat"], rd["qt"], rd["qr"], w_az=rd["w"], image=out, M=M)
 
-    # warm-up
-    for rd in radars:
-        out = torch.empty(rd["plan"].n_pixels, dtype=torch.complex64).pin_memory()
-        t = submit(rd, 512, out)
-        srv.wait(t, 60000)
-        srv.release(t)
+    def make_server(chunk, quantum):
+        srv = sar.Server(hbm_budget=8 << 30, max_inflight=64, queue_capacity=4096, chunk_pulses=chunk,
+                         quantum_mupdates=quantum)
+        for rd in radars:  # warm-up
+            out = torch.empty(rd["plan"].n_pixels, dtype=torch.complex64).pin_memory()
+            t = submit(srv, rd, 512, out)
+            srv.wait(t, 60000)
+            srv.release(t)
+        return srv
+
+    def poisson(srv):
+        lat, lock = [], threading.Lock()  # (radar, chirps, latency ms)
+        t_start = time.perf_counter()
+
+        def radar_thread(k):
+            r = np.random.Generator(np.random.PCG64(seed * 10 + k))
+            mine = []
+            t_next = t_start
+            while True:
+                t_next += r.exponential(1.0 / rates[k])
+                if t_next - t_start > duration_s:
+                    break
+                time.sleep(max(0.0, t_next - time.perf_counter()))
+                M = int(r.integers(256, 2049))
+                out = torch.empty(radars[k]["plan"].n_pixels, dtype=torch.complex64).pin_memory()
+                mine.append((submit(srv, radars[k], M, out), M, out))
+            for t, M, _ in mine:
+                srv.wait(t, 120000)
+                rc, state, _, ms = srv.poll(t)
+                with lock:
+                    lat.append((k, M, ms))
+                srv.release(t)
+
+        threads = [threading.Thread(target=radar_thread, args=(k,)) for k in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        wall = time.perf_counter() - t_start
+        return lat, wall
+
+    sweep = []
+    per_radar = {}
+    for chunk, quantum in SERVED_CONFIGS:
+        srv = make_server(chunk, quantum)
+        r0 = srv.stats().rounds
+        rec, wall = poisson(srv)
+        rounds = int(srv.stats().rounds - r0)
+        srv.close()
+        lat = [ms for _, _, ms in rec]
+        e = {"chunk_pulses": chunk, "quantum_mupdates": quantum, "frames": len(lat),
+             "frames_per_s": len(lat) / wall, "latency_p50_ms": float(np.percentile(lat, 50)),
+             "latency_p99_ms": float(np.percentile(lat, 99)),
+             "latency_max_ms": float(max(lat)), "rounds": rounds}
+        sweep.append(e)
+        # per radar (one image size each): latency against the acquisition
+        # time of the frame, M x PRI (the paper's real-time criterion)
+        per_radar[(chunk, quantum)] = [
+            {"image_side": sides[k], "frames": len(v),
+             "latency_p50_ms": float(np.percentile([x[2] for x in v], 50)),
+             "latency_p99_ms": float(np.percentile([x[2] for x in v], 99)),
+             "max_latency_over_acquisition": float(max(x[2] / (x[1] * radars[k]["wl"].radar.pri * 1e3)
+                                                       for x in v))}
+            for k in range(4) for v in [[x for x in rec if x[0] == k]] if v]
+    best = min(sweep, key=lambda e: e["latency_p99_ms"])
     # saturated: all frames queued at once vs sequential per-frame processing
-    # (three alternating repetitions of each, medians)
+    # (three alternating repetitions of each, medians), best-p99 configuration
+    srv = make_server(best["chunk_pulses"], best["quantum_mupdates"])
     frames = [(int(rng.integers(0, 4)), int(rng.integers(256, 2049))) for _ in range(n_saturate)]
     outs = [torch.empty(radars[k]["plan"].n_pixels, dtype=torch.complex64).pin_memory()
             for k, _ in frames]
@@ -496,7 +562,7 @@ def bench_served(dev, duration_s=3.0, seed=7, n_saturate=40):
     for _ in range(3):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        tickets = [submit(radars[k], M, o) for (k, M), o in zip(frames, outs)]
+        tickets = [submit(srv, radars[k], M, o) for (k, M), o in zip(frames, outs)]
         for t in tickets:
             assert srv.wait(t, 120000) == sar.SAR_OK
         ts_served.append(time.perf_counter() - t0)
@@ -507,51 +573,26 @@ def bench_served(dev, duration_s=3.0, seed=7, n_saturate=40):
             rd = radars[k]
             rd["plan"].form_image_host(rd["beat"][:M], rd["qt"][:M], rd["qr"][:M], o, w_az=rd["w"][:M])
         ts_plain.append(time.perf_counter() - t0)
+    srv.close()
     t_served, t_plain = statistics.median(ts_served), statistics.median(ts_plain)
     err = max(float(np.linalg.norm(a.numpy() - b.numpy()) / np.linalg.norm(b.numpy()))
               for a, b in zip(outs, plain_outs))
-    # Poisson arrivals from 4 radar threads
-    lat, lock = [], threading.Lock()
-    t_start = time.perf_counter()
-
-    def radar_thread(k):
-        r = np.random.Generator(np.random.PCG64(seed * 10 + k))
-        mine = []
-        t_next = t_start
-        while True:
-            t_next += r.exponential(1.0 / rates[k])
-            if t_next - t_start > duration_s:
-                break
-            time.sleep(max(0.0, t_next - time.perf_counter()))
-            M = int(r.integers(256, 2049))
-            out = torch.empty(radars[k]["plan"].n_pixels, dtype=torch.complex64).pin_memory()
-            mine.append((submit(radars[k], M, out), out))
-        for t, _ in mine:
-            srv.wait(t, 120000)
-            rc, state, _, ms = srv.poll(t)
-            with lock:
-                lat.append(ms)
-            srv.release(t)
-
-    threads = [threading.Thread(target=radar_thread, args=(k,)) for k in range(4)]
-    for th in threads:
-        th.start()
-    for th in threads:
-        th.join()
-    wall = time.perf_counter() - t_start
-    stats = srv.stats()
-    srv.close()
-    return {"radars": 4, "rates_hz": [float(x) for x in rates], "frames": len(lat),
-            "frames_per_s": len(lat) / wall, "latency_p50_ms": float(np.percentile(lat, 50)),
-            "latency_p99_ms": float(np.percentile(lat, 99)), "latency_max_ms": float(max(lat)),
+    return {"radars": 4, "rates_hz": [float(x) for x in rates],
+            "chunk_pulses": best["chunk_pulses"], "quantum_mupdates": best["quantum_mupdates"],
+            "frames": best["frames"], "frames_per_s": best["frames_per_s"],
+            "latency_p50_ms": best["latency_p50_ms"], "latency_p99_ms": best["latency_p99_ms"],
+            "latency_max_ms": best["latency_max_ms"], "rounds": best["rounds"],
             "saturated_frames": n_saturate, "saturated_served_frames_per_s": n_saturate / t_served,
             "saturated_plain_frames_per_s": n_saturate / t_plain,
             "saturated_speedup": t_plain / t_served,
-            "max_rel_l2_served_vs_plain": err, "rounds": int(stats.rounds),
+            "max_rel_l2_served_vs_plain": err, "sweep": sweep,
+            "per_radar": per_radar[(best["chunk_pulses"], best["quantum_mupdates"])],
             "config": "4 radars, images 256^2/512^2/768^2/1024^2 at 2.5 cm, 256-2048 chirps x 4 Rx "
                       "x 512 samples per frame, FP16 profiles, Poisson arrivals at the given rates "
-                      "for 3 s; latency = submit to image in pinned host memory; plain = the same "
-                      "frames one by one through sar_form_image_host"}
+                      f"for {duration_s:.0f} s per round configuration (same seeded arrivals); latency "
+                      "= submit to image in pinned host memory; headline = the configuration with "
+                      "the lowest p99; plain = the same frames one by one through "
+                      "sar_form_image_host"}
 
 
 def run_ours(args):

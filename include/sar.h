@@ -410,15 +410,17 @@ int sar_batch_get_class(const sar_batch *batch, int32_t index, sar_batch_class *
  * A server owns one worker thread and three CUDA streams on the device that
  * is current at creation.  Each request is one frame (sar_request): its beat
  * cube, w_sar and trajectory are copied to the device when it is admitted,
- * range-compressed, then backprojected in rounds: every round is ONE
- * persistent batched launch over the next chunk_pulses chirps of every
- * active request, accumulated into the request's device-resident image.
+ * range-compressed, then backprojected in rounds: every round is one batched
+ * launch (sar_batch_launch) over the next chunk of every active request --
+ * chunk_pulses chirps, or fewer when quantum_mupdates bounds each request's
+ * work per round -- accumulated into the request's device-resident image.
  * Requests that arrive while a round runs join the first round launched after
  * their upload and range compression have completed; finished ones leave.
- * Larger chunk_pulses means fewer rounds (less per-round cost); a value at
- * least the frames' chirp count (one round per frame) gave the best
- * throughput and no worse latency on frames of 256-2048 chirps.  Admission is bounded by max_inflight and by an HBM budget (one
- * device pool allocated at creation and sub-allocated per request); a request
+ * Larger chunks mean fewer rounds (less per-round cost), but a newcomer waits
+ * for the round in flight: chunk_pulses and quantum_mupdates trade throughput
+ * against the latency tail.  Admission is bounded by max_inflight and by an
+ * HBM budget (one device pool allocated at creation and sub-allocated per
+ * request); a request
  * waits in arrival order until its buffers fit.  A request's image equals its
  * stand-alone sar_range_compress + sar_backproject result up to FP32
  * summation order.
@@ -438,8 +440,12 @@ typedef struct sar_server_config {
     size_t hbm_budget_bytes;  /* device pool for request buffers (>= 1 MiB) */
     int32_t max_inflight;     /* requests on the device at once (1..4096) */
     int32_t queue_capacity;   /* submitted, not yet admitted (SAR_EAGAIN beyond) */
-    int32_t chunk_pulses;     /* chirps per request per round */
-    int32_t reserved;
+    int32_t chunk_pulses;     /* chirps per request per round (at most) */
+    int32_t quantum_mupdates; /* 0, or a work quantum per request and round in millions of
+                                 pixel x chirp x Rx updates: a request advances by at most
+                                 ceil(quantum / (pixels x Rx)) chirps per round, so frames
+                                 smaller than the quantum finish in their first round while
+                                 larger ones share the following rounds with newcomers */
 } sar_server_config;
 
 typedef struct sar_request {

@@ -89,7 +89,7 @@ class BatchClass(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("chunk_pulses", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("quantum_mupdates", ctypes.c_int32)]
 
 
 class RequestDesc(ctypes.Structure):
@@ -487,11 +487,12 @@ class Server:
     referenced until the request is released."""
 
     def __init__(self, hbm_budget: int, max_inflight: int = 64, queue_capacity: int = 1024,
-                 chunk_pulses: int = 2048):
+                 chunk_pulses: int = 2048, quantum_mupdates: int = 0):
         self._lib = load_library()
         self._s = None
         cfg = ServerConfig(hbm_budget_bytes=hbm_budget, max_inflight=max_inflight,
-                           queue_capacity=queue_capacity, chunk_pulses=chunk_pulses, reserved=0)
+                           queue_capacity=queue_capacity, chunk_pulses=chunk_pulses,
+                           quantum_mupdates=quantum_mupdates)
         h = ctypes.c_void_p()
         _check(self._lib.sar_server_create(ctypes.byref(cfg), ctypes.byref(h)), "sar_server_create")
         self._s = h

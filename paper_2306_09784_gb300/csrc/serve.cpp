@@ -5,10 +5,11 @@
 //    w_sar, trajectory) and the device -> host copy of finished images;
 //  * range-compression stream: range compression of newly admitted requests,
 //    overlapping the backprojection rounds already running;
-//  * round stream: backprojection rounds.  A round is ONE persistent batched
-//    launch over the next sub-aperture chunk (chunk_pulses chirps) of every
-//    active request, accumulated into its device-resident image.  Requests
-//    that arrive while a round runs join the next round; finished ones leave.
+//  * round stream: backprojection rounds.  A round is ONE batched launch over
+//    the next sub-aperture chunk of every active request (chunk_pulses
+//    chirps, or fewer when a work quantum per request and round is set),
+//    accumulated into its device-resident image.  Requests that arrive while
+//    a round runs join the next round; finished ones leave.
 // Admission is bounded by slots (max_inflight) and by an HBM budget: one
 // device pool allocated at creation and sub-allocated first-fit; a request
 // waits in the queue until its buffers fit.  Each request's image equals its
@@ -16,6 +17,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -248,13 +250,21 @@ int launch_round(sar_server *s, std::vector<Request *> &work, bool *launched) {
     int rc = sar_batch_clear(b);
     if (rc) return rc;
     const int chunk = s->cfg.chunk_pulses;
+    const double quantum = 1e6 * (double)s->cfg.quantum_mupdates;
     for (Request *q : part) {
         if (!q->joined) {
             if (cudaStreamWaitEvent(s->round_s, q->rc_ev, 0) != cudaSuccess) return SAR_ECUDA;
             q->joined = true;
         }
         const int m0 = q->next_pulse;
-        const int cnt = std::min(chunk, q->r.M - m0);
+        int cnt = std::min(chunk, q->r.M - m0);
+        if (quantum > 0) {
+            // at most about `quantum` pixel x chirp x Rx updates of this
+            // request per round: a small frame completes in its first round,
+            // a large one advances by a share and leaves room for newcomers
+            const double per_chirp = (double)q->n_pixels * q->n_rx;
+            cnt = (int)std::min<double>(cnt, std::max(1.0, std::ceil(quantum / per_chirp)));
+        }
         const int R = q->n_rx;
         const size_t rows0 = (size_t)m0 * R;
         const char *samples;
@@ -402,7 +412,7 @@ int sar_server_create(const sar_server_config *cfg, sar_server **out) {
     if (!cfg || !out) return SAR_EINVAL;
     *out = nullptr;
     if (cfg->hbm_budget_bytes < (1u << 20) || cfg->max_inflight < 1 || cfg->max_inflight > 4096 ||
-        cfg->queue_capacity < 1 || cfg->chunk_pulses < 1)
+        cfg->queue_capacity < 1 || cfg->chunk_pulses < 1 || cfg->quantum_mupdates < 0)
         return SAR_EINVAL;
     sar_server *s = new (std::nothrow) sar_server();
     if (!s) return SAR_ENOMEM;

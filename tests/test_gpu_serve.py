@@ -91,13 +91,15 @@ def test_host_image_mapped_and_pageable_match_the_device_image():
     srv.close()
 
 
-def test_each_result_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("chunk,quantum", [(48, 0), (4096, 2)], ids=["chunk48", "quantum2M"])
+def test_each_result_same_alone_and_in_the_mix(chunk, quantum):
     """Twelve frames of different radars (plans, Rx counts, storages, sizes)
     submitted together and while others run: every image equals the same
-    frame imaged alone, within the FP32 summation-order tolerance."""
+    frame imaged alone, within the FP32 summation-order tolerance; with
+    fixed chunks and with a work quantum per request and round."""
     import paper_2306_09784_gb300 as sar
     frames = _frames(12)
-    srv = sar.Server(hbm_budget=1 << 30, chunk_pulses=48)
+    srv = sar.Server(hbm_budget=1 << 30, chunk_pulses=chunk, quantum_mupdates=quantum)
     tickets = [_submit(srv, f) for f in frames[:6]]
     time.sleep(0.002)  # the rest arrive while the first rounds run
     tickets += [_submit(srv, f) for f in frames[6:]]
