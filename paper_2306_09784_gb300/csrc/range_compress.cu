@@ -528,22 +528,21 @@ __host__ __device__ constexpr int split_region(int n2, int os) {
     return base + (((want - base) % 16) + 16) % 16;
 }
 
-// Job of row group g: the launch's single job, or (batched form) the job of
-// the table whose groups [group_begin[j], group_begin[j + 1]) hold g, with g
-// made local to it.
-__device__ __forceinline__ const RcSplitArgs &split_job(const RcSplitArgs &single, const RcSplitBatch &t,
-                                                        long long &g) {
-    if (t.jobs == nullptr) return single;
+// Batched form: the job of the table whose row groups
+// [group_begin[j], group_begin[j + 1]) hold g, with g made local to it.
+__device__ __forceinline__ int split_job(const RcSplitBatch &t, long long &g) {
     int lo = 0, hi = t.n_jobs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (t.group_begin[mid] <= g) lo = mid; else hi = mid - 1;
     }
     g -= t.group_begin[lo];
-    return t.jobs[lo];
+    return lo;
 }
 
-template <int SGN, int MODE, int N2>
+// BATCH: jobs from the table (fields loaded per row group); otherwise the
+// single job a0, whose fields stay kernel parameters (constant bank).
+template <int SGN, int MODE, int N2, bool BATCH>
 __global__ void __launch_bounds__(kSplitThreads, 2) range_compress_split(RcSplitArgs a0, RcSplitBatch tab,
                                                                          long long n_groups) {
     constexpr int N = 32 * N2;
@@ -562,23 +561,13 @@ __global__ void __launch_bounds__(kSplitThreads, 2) range_compress_split(RcSplit
     float2 *xrow = xbuf + lrow * os * REG;          // the row's first region
     const int sh_os = 31 - __clz(os);
 
-    for (long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
-        long long gl = g;
-        const RcSplitArgs &a = split_job(a0, tab, gl);
+    // one row group of job a (gl: the group's index within the job)
+    auto group = [&](const RcSplitArgs &a, long long gl) {
         const float2 *pre = a.pre + (size_t)s * N + j;  // w_r[n] W^(n s) at n = N2 n1 + j
         const float2 *twd = a.twd + j;                   // W_N^(j k1) at [k1][j]
         const long long row = gl * RPC + lrow;
         const bool active = row < a.rows;
         const float2 *x = a.beat + (active ? row : 0) * (long long)N;
-        // L2 prefetch of the row this thread group handles next (one 128-byte
-        // line per thread)
-        if (g + gridDim.x < n_groups) {
-            long long gn = g + gridDim.x;
-            const RcSplitArgs &an = split_job(a0, tab, gn);
-            const long long nrow = gn * RPC + lrow;
-            if (nrow < an.rows && rem * 16 < N)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(an.beat + nrow * (long long)N + rem * 16));
-        }
         float2 v[32];
 #pragma unroll
         for (int n1 = 0; n1 < 32; ++n1) {
@@ -665,6 +654,29 @@ __global__ void __launch_bounds__(kSplitThreads, 2) range_compress_split(RcSplit
             }
             __syncthreads();  // the regions and row_max are rewritten by the next row
         }
+    };
+
+    for (long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
+        // L2 prefetch of the row this thread group handles next (one 128-byte
+        // line per thread)
+        const long long gn = g + gridDim.x;
+        if constexpr (BATCH) {
+            if (gn < n_groups) {
+                long long gnl = gn;
+                const RcSplitArgs &an = tab.jobs[split_job(tab, gnl)];
+                const long long nrow = gnl * RPC + lrow;
+                if (nrow < an.rows && rem * 16 < N)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(an.beat + nrow * (long long)N + rem * 16));
+            }
+            long long gl = g;
+            const RcSplitArgs aj = tab.jobs[split_job(tab, gl)];
+            group(aj, gl);
+        } else {
+            const long long nrow = gn * RPC + lrow;
+            if (nrow < a0.rows && rem * 16 < N)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a0.beat + nrow * (long long)N + rem * 16));
+            group(a0, g);
+        }
     }
 }
 
@@ -719,9 +731,12 @@ cudaError_t launch_rc(const RcArgs &a, cudaStream_t s) {
 
 template <int SGN, int MODE>
 cudaError_t launch_split(const RcSplitArgs &a, const RcSplitBatch &tab, long long groups, cudaStream_t s) {
-    auto kern = a.N2 == 32   ? range_compress_split<SGN, MODE, 32>
-                : a.N2 == 16 ? range_compress_split<SGN, MODE, 16>
-                             : range_compress_split<SGN, MODE, 8>;
+    auto kern = tab.jobs ? (a.N2 == 32   ? range_compress_split<SGN, MODE, 32, true>
+                            : a.N2 == 16 ? range_compress_split<SGN, MODE, 16, true>
+                                         : range_compress_split<SGN, MODE, 8, true>)
+                         : (a.N2 == 32   ? range_compress_split<SGN, MODE, 32, false>
+                            : a.N2 == 16 ? range_compress_split<SGN, MODE, 16, false>
+                                         : range_compress_split<SGN, MODE, 8, false>);
     const int rpc = kSplitThreads / (a.N2 * a.os);
     const long long n_groups = tab.jobs ? groups : (a.rows + rpc - 1) / rpc;
     if (n_groups == 0) return cudaSuccess;
