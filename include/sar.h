@@ -171,7 +171,7 @@ typedef struct sar_plan_info {
     int32_t n_bins;             /* samples per stored range profile = crop_hi - crop_lo + 1 */
     int32_t crop_lo, crop_hi;
     int64_t n_pixels;           /* image size in complex64 values */
-    int32_t n_tiles;            /* pixel tiles of 1024 reconstruction points */
+    int32_t n_tiles;            /* pixel tiles of 1024 reconstruction points (slots) */
     int32_t window_bins;        /* bins staged per (tile, chirp, Rx) */
     int32_t pulses_per_block;   /* chirps staged per pipeline step */
     int32_t bp_ctas;            /* persistent backprojection grid size */
@@ -180,6 +180,7 @@ typedef struct sar_plan_info {
     size_t device_bytes;        /* device memory the plan owns */
     int32_t rx_group;           /* Rx channels per inner-loop group of the launch shape */
     int32_t regs_ctas_per_sm;   /* CTAs per SM the launch's registers are sized for */
+    int32_t tile_w, tile_h;     /* pixel tile of a Cartesian plan (0, 0: point list) */
 } sar_plan_info;
 
 /*
@@ -394,6 +395,8 @@ typedef struct sar_batch_class {
     int32_t regs_ctas_per_sm;  /* CTAs per SM the launch's registers are sized for (2) */
     int64_t units;             /* (tile, pulse block) work units */
     double updates;            /* pixel slots x chirps x Rx */
+    double tuned_ms;           /* the class launch (with its fix-up) at the chosen block, as timed by
+                                  sar_batch_autotune; 0 before it runs */
 } sar_batch_class;
 
 int sar_batch_num_classes(const sar_batch *batch, int32_t *n_classes);
@@ -510,17 +513,20 @@ int sar_form_image_host(sar_plan *plan, const void *beat_host, int32_t M,
 
 /*
  * Autotuner of the backprojection launch shape (no counterpart in the paper):
- * times sar_backproject on these inputs for each candidate shape (Rx group:
- * the plan's default and the next smaller divisor of n_rx; CTAs per SM the
- * registers are sized for: 2 or 3; chirps per pipeline block: the largest
- * that fits that many CTAs' shared memory, 2/3 and 1/2 of it) and keeps the
- * fastest in the plan (see sar_plan_get_info).  The choice is also
- * remembered for the process, keyed by device, Rx count, staged window
- * length, profile storage, and max_pulses and tile count rounded up to
- * powers of two: plans created later with the same key start from it.
- * image_dev is overwritten.  Blocks until the timing runs on `stream`
- * finish.  Results of later calls do not depend on the choice beyond FP32
- * summation order.
+ * times sar_backproject on these inputs for each candidate shape (pixel
+ * tile, Cartesian grids only: 32 x 32, 64 x 16 and 16 x 64 pixels, see
+ * sar_plan_set_tile_shape; then per tiling the Rx group: the plan's default
+ * and the next smaller divisor of n_rx; CTAs per SM the registers are sized
+ * for: 2 or 3; chirps per pipeline block: the largest that fits that many
+ * CTAs' shared memory, 2/3 and 1/2 of it) and keeps the fastest in the plan
+ * (see sar_plan_get_info).  The choice is also remembered for the process,
+ * keyed by device, Rx count, the staged window length and tile count of the
+ * plan's first tiling (tile count and max_pulses rounded up to powers of
+ * two) and profile storage: plans created later with the same key start
+ * from it.  image_dev is overwritten.  Blocks until the timing runs on
+ * `stream` finish.  Results of later calls do not depend on the choice
+ * beyond FP32 rounding (summation order, and pixel offsets taken from
+ * another tile reference).
  */
 int sar_plan_autotune(sar_plan *plan, const void *prof_dev, int32_t M, const double *q_tx_dev,
                       const double *q_rx_dev, void *image_dev, void *stream);
@@ -537,6 +543,26 @@ int sar_plan_autotune(sar_plan *plan, const void *prof_dev, int32_t M, const dou
  * against calls that use the plan.
  */
 int sar_plan_set_launch(sar_plan *plan, int32_t rx_group, int32_t regs_ctas_per_sm, int32_t pulses_per_block);
+
+/*
+ * Pixel tile shape of a Cartesian plan: tiles of tile_w x (1024 / tile_w)
+ * pixels, tile_w = 16, 32 (the default) or 64.  The backprojection stages,
+ * per (tile, chirp, Rx), the bins the tile can reach (Alg. 2's
+ * interpolation window), sized by the tile's circumradius: a square tile
+ * needs the shortest window for its 1024 points, an elongated one can fit a
+ * narrow grid with fewer empty slots.  The first use of a width builds and
+ * uploads its tiling (tile offsets, output indices, split-tile partial sums:
+ * about 20 bytes per grid pixel plus 8 KB per tile and 48 KB per SM, within
+ * the plan's HBM budget); every tiling a plan has built stays allocated until
+ * sar_plan_destroy, so launches and batches that captured an earlier tiling
+ * remain valid.  The launch shape keeps its Rx group and register budget
+ * where they fit and takes the largest pulse block that fits two CTAs per SM.
+ * SAR_EINVAL for a point-list plan (its tiles are 1024 Morton-ordered points)
+ * or another width; SAR_ENOMEM if the tiling does not fit the budget.  On
+ * error the plan is unchanged.  Not thread-safe against calls that use the
+ * plan.
+ */
+int sar_plan_set_tile_shape(sar_plan *plan, int32_t tile_w);
 
 /*
  * Waits for the plan's device work and reports (then clears) kernel-side

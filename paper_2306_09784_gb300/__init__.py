@@ -33,6 +33,7 @@ EXPORTS = (
     "sar_release", "sar_server_get_stats", "sar_plan_autotune", "sar_plan_set_launch",
     "sar_alu_peaks", "sar_polar_grid", "sar_doppler_offsets", "sar_batch_autotune",
     "sar_batch_num_classes", "sar_batch_get_class", "sar_batch_check_errors", "sar_batch_add_frame",
+    "sar_plan_set_tile_shape",
 )
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 
@@ -71,6 +72,7 @@ class PlanInfo(ctypes.Structure):
         ("bp_ctas", ctypes.c_int32), ("bins_per_metre", ctypes.c_double),
         ("cycles_per_bin", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
         ("rx_group", ctypes.c_int32), ("regs_ctas_per_sm", ctypes.c_int32),
+        ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
     ]
 
 
@@ -83,7 +85,7 @@ class BatchClass(ctypes.Structure):
     _fields_ = [("rx_group", ctypes.c_int32), ("fp16", ctypes.c_int32), ("n_jobs", ctypes.c_int32),
                 ("pulses_per_block", ctypes.c_int32), ("ctas", ctypes.c_int32),
                 ("regs_ctas_per_sm", ctypes.c_int32), ("units", ctypes.c_int64),
-                ("updates", ctypes.c_double)]
+                ("updates", ctypes.c_double), ("tuned_ms", ctypes.c_double)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -160,6 +162,7 @@ def load_library(path: str = LIB_PATH):
     lib.sar_batch_get_class.argtypes = [vp, i32, ctypes.POINTER(BatchClass)]
     lib.sar_batch_check_errors.argtypes = [vp, ctypes.POINTER(i32)]
     lib.sar_batch_add_frame.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, i32]
+    lib.sar_plan_set_tile_shape.argtypes = [vp, i32]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if name not in ("sar_plan_destroy", "sar_status_string", "sar_batch_destroy",
@@ -379,10 +382,16 @@ class Plan:
         """The backprojection launch shape the plan uses now."""
         _check(self._lib.sar_plan_get_info(self._plan, ctypes.byref(self.info)),
                "sar_plan_get_info")
-        return {"rx_group": int(self.info.rx_group),
+        return {"tile": [int(self.info.tile_w), int(self.info.tile_h)],
+                "rx_group": int(self.info.rx_group),
                 "regs_ctas_per_sm": int(self.info.regs_ctas_per_sm),
                 "pulses_per_block": int(self.info.pulses_per_block),
                 "bp_ctas": int(self.info.bp_ctas)}
+
+    def set_tile_shape(self, tile_w: int) -> dict:
+        """Cartesian plans: tiles of tile_w x (1024 // tile_w) pixels (16, 32, 64)."""
+        _check(self._lib.sar_plan_set_tile_shape(self._plan, tile_w), "sar_plan_set_tile_shape")
+        return self.launch_shape()
 
     def set_launch(self, rx_group: int, regs_ctas_per_sm: int, pulses_per_block: int) -> dict:
         """Install an explicit launch shape (e.g. one saved after autotune)."""

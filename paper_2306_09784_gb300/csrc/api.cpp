@@ -36,7 +36,7 @@ struct sar_plan {
     int n_tiles = 0;
     int L = 0, Mb = 0, rg = 1;
     size_t bp_smem = 0;
-    int num_sms = 0, ctas_per_sm = 0, G = 0, seg_cap = 0, minb = 2;
+    int num_sms = 0, ctas_per_sm = 0, G = 0, minb = 2;
     size_t partial_slots = 0;  // partial-sum tile slots allocated
     float fd_max = 0.f;
     // device memory owned by the plan
@@ -62,6 +62,24 @@ struct sar_plan {
     cudaEvent_t ev_start = nullptr, ev_chunk[2] = {nullptr, nullptr}, ev_traj = nullptr;
     size_t budget = 0, used = 0;
     std::vector<void *> allocs;
+    // Pixel tilings built so far; the current one is mirrored in n_tiles, L,
+    // d_pix, d_out, d_tiles, d_partial and partial_slots.  A Cartesian grid
+    // can be tiled 16 x 64, 32 x 32 or 64 x 16 (tile width tw); a point list
+    // has its one Morton tiling (tw = 0).  Buffers of every tiling live until
+    // the plan is destroyed, so launches in flight and batches that captured
+    // an earlier tiling stay valid.
+    struct Tiling {
+        int tw = 0, n_tiles = 0, L = 0;
+        size_t partial_slots = 0;
+        float2 *d_pix = nullptr;
+        int *d_out = nullptr;
+        TileInfo *d_tiles = nullptr;
+        float2 *d_partial = nullptr;
+    };
+    std::vector<Tiling> tilings;
+    int tile_w = 0;
+    sar_grid grid{};  // the Cartesian grid (pixels_xy = null), for re-tiling
+    int key_L = 0, key_tiles = 0;  // window and tile count of the first tiling (remembered-shape key)
 };
 
 // Requests of a batch are grouped into classes with the same Rx group and
@@ -82,6 +100,7 @@ struct BatchClass {
 // (0 = each request's plan's own).
 struct ClassShape {
     int mb = 0;
+    float ms = 0.f;  // its launch time as measured by sar_batch_autotune (0: not tuned)
 };
 
 struct sar_batch {
@@ -232,7 +251,7 @@ int apply_launch(sar_plan *pl, int rg, int minb, int Mb) {
 // storage, and max_pulses and tile count rounded up to powers of two.
 using ShapeKey = std::tuple<int, int, int, int, int, int>;
 struct Shape {
-    int rg, minb, Mb;
+    int rg, minb, Mb, tw;
 };
 std::mutex g_shape_mu;
 std::map<ShapeKey, Shape> g_shapes;
@@ -243,15 +262,18 @@ int pow2_ceil(long long v) {
     return e;
 }
 
+// Keyed by the plan's first tiling, whatever tiling it uses now.
 ShapeKey shape_key(const sar_plan *pl) {
-    return ShapeKey{pl->device, pl->p.n_rx, pl->L, pl->fp16 ? 1 : 0, pow2_ceil(pl->p.max_pulses),
-                    pow2_ceil(pl->n_tiles)};
+    return ShapeKey{pl->device, pl->p.n_rx, pl->key_L, pl->fp16 ? 1 : 0, pow2_ceil(pl->p.max_pulses),
+                    pow2_ceil(pl->key_tiles)};
 }
 
 void remember_shape(const sar_plan *pl) {
     std::lock_guard<std::mutex> g(g_shape_mu);
-    g_shapes[shape_key(pl)] = Shape{pl->rg, pl->minb, pl->Mb};
+    g_shapes[shape_key(pl)] = Shape{pl->rg, pl->minb, pl->Mb, pl->tile_w};
 }
+
+int plan_retile(sar_plan *pl, int tw);
 
 // Start a new plan from a remembered shape, if there is one that fits.
 void recall_shape(sar_plan *pl) {
@@ -262,7 +284,9 @@ void recall_shape(sar_plan *pl) {
         if (it == g_shapes.end()) return;
         sh = it->second;
     }
-    apply_launch(pl, sh.rg, sh.minb, sh.Mb);  // the plan keeps its default shape if this fails
+    // the plan keeps its default tiling and shape where these fail
+    if (sh.tw != pl->tile_w && plan_retile(pl, sh.tw) != SAR_OK) return;
+    apply_launch(pl, sh.rg, sh.minb, sh.Mb);
 }
 
 // Modified Bessel I0 from its power series.
@@ -341,19 +365,26 @@ void finish_tile(HostTiles &ht, int t, const std::vector<double> &xs, const std:
     }
 }
 
-int build_tiles(const sar_grid *g, HostTiles &ht, int64_t *n_pixels) {
+// Tiles of kTilePx reconstruction points.  Cartesian grid: rectangles of
+// tw x (kTilePx / tw) pixels, row-major over the grid; slot = ly tw + lx, so
+// thread t of a CTA owns slots t + kBpThreads j.  Point list: Morton order,
+// kTilePx consecutive points per tile (tw is ignored).
+int build_tiles(const sar_grid *g, HostTiles &ht, int64_t *n_pixels, int tw) {
     if (g->pixels_xy == nullptr) {
         if (g->nx <= 0 || g->ny <= 0 || !std::isfinite(g->x0) || !std::isfinite(g->y0) ||
             !std::isfinite(g->dx) || !std::isfinite(g->dy))
             return SAR_EINVAL;
+        if (tw <= 0 || kTilePx % tw != 0) return SAR_EINVAL;
+        const int th = kTilePx / tw;
         const int64_t np = (int64_t)g->nx * g->ny;
         if (np > (int64_t)1 << 30) return SAR_EINVAL;
         *n_pixels = np;
-        const int ntx = (g->nx + 31) / 32, nty = (g->ny + 31) / 32;
+        const int ntx = (g->nx + tw - 1) / tw, nty = (g->ny + th - 1) / th;
         const int T = ntx * nty;
         ht.pix.assign((size_t)T * kTilePx, make_float2(0.f, 0.f));
         ht.out.assign((size_t)T * kTilePx, -1);
         ht.tiles.assign(T, TileInfo{});
+        ht.rho_max = 0;
         std::vector<double> xs, ys;
         std::vector<int> oi;
         for (int ty = 0; ty < nty; ++ty)
@@ -362,11 +393,9 @@ int build_tiles(const sar_grid *g, HostTiles &ht, int64_t *n_pixels) {
                 xs.clear();
                 ys.clear();
                 oi.clear();
-                // slot = ly * 32 + lx: thread t owns column t % 32, rows t / 32 + 8 j
-                std::vector<int> slot_of;
-                for (int ly = 0; ly < 32; ++ly)
-                    for (int lx = 0; lx < 32; ++lx) {
-                        const int ix = tx * 32 + lx, iy = ty * 32 + ly;
+                for (int ly = 0; ly < th; ++ly)
+                    for (int lx = 0; lx < tw; ++lx) {
+                        const int ix = tx * tw + lx, iy = ty * th + ly;
                         const bool v = ix < g->nx && iy < g->ny;
                         xs.push_back(v ? g->x0 + ix * g->dx : 0.0);
                         ys.push_back(v ? g->y0 + iy * g->dy : 0.0);
@@ -483,6 +512,100 @@ int validate_grid(const sar_grid *g) {
     return (g->n_pixels <= 0 || g->n_pixels > (int64_t)1 << 30) ? SAR_EINVAL : SAR_OK;
 }
 
+// Staged window length of a tiling: it covers a1 (d0 -+ 2 rho) -+ fd_max
+// plus guards for every tile (two-way range spread of a disc of radius rho),
+// and the per-tile window constants that depend on it.
+int window_length(const sar_plan *pl, HostTiles &ht) {
+    const double span = 4.0 * ht.rho_max * pl->a1 + 2.0 * std::ceil((double)pl->fd_max);
+    int L = (int)std::ceil(span) + 2 * kGuardBins + 4;
+    L = (L + 3) & ~3;
+    for (TileInfo &ti : ht.tiles) {
+        const double o_allow = ((double)(L - 3 - 2 * kGuardBins) - 2.0 * pl->fd_max - 4.0 * ti.rho * pl->a1) /
+                               (2.0 * pl->a1);
+        ti.o_allow = (float)o_allow;
+        ti.klo_off = (float)(pl->a1 * (2.0 * ti.rho + o_allow) + pl->fd_max);
+    }
+    return L;
+}
+
+// Largest pulse block whose shared memory fits two CTAs per SM.
+int default_block(const sar_plan *pl, int L) {
+    const int R = pl->p.n_rx;
+    const size_t per_pulse = bp_smem_bytes(1, R, L, pl->fp16);
+    int Mb = (int)std::min<size_t>(kMaxPulsesPerBlock, std::max<size_t>(1, kBpSmemTarget / per_pulse));
+    while (Mb > 1 && bp_smem_bytes(Mb, R, L, pl->fp16) > kBpSmemTarget) --Mb;
+    return Mb;
+}
+
+// Upload a tiling and its split-tile partial sums, and make it current.  The
+// partial sums cover any persistent grid G of 1 to 3 CTAs per SM: a launch
+// needs G seg_max slots with seg_max <= n_tiles / G + 2.
+int install_tiling(sar_plan *pl, const HostTiles &ht, int tw, int L) {
+    sar_plan::Tiling t;
+    t.tw = tw;
+    t.L = L;
+    t.n_tiles = (int)ht.tiles.size();
+    t.partial_slots = (size_t)t.n_tiles + 6u * (size_t)pl->num_sms;
+    int rc = upload(pl, ht.pix, &t.d_pix);
+    if (!rc) rc = upload(pl, ht.out, &t.d_out);
+    if (!rc) rc = upload(pl, ht.tiles, &t.d_tiles);
+    if (!rc) {
+        void *q = nullptr;
+        rc = dev_alloc(pl, t.partial_slots * kTilePx * sizeof(float2), &q);
+        t.d_partial = (float2 *)q;
+    }
+    if (rc) return rc;  // what was allocated is freed with the plan
+    pl->tilings.push_back(t);
+    return SAR_OK;
+}
+
+void use_tiling(sar_plan *pl, const sar_plan::Tiling &t) {
+    pl->tile_w = t.tw;
+    pl->n_tiles = t.n_tiles;
+    pl->L = t.L;
+    pl->partial_slots = t.partial_slots;
+    pl->d_pix = t.d_pix;
+    pl->d_out = t.d_out;
+    pl->d_tiles = t.d_tiles;
+    pl->d_partial = t.d_partial;
+}
+
+// Switch a Cartesian plan to tiles tw pixels wide (16, 32 or 64), building
+// the tiling on first use.  The launch shape keeps its Rx group and register
+// budget where they fit; the pulse block becomes the largest that fits two
+// CTAs per SM.  On failure the plan is unchanged.
+int plan_retile(sar_plan *pl, int tw) {
+    if (pl->tile_w == 0) return SAR_EINVAL;  // point list: one Morton tiling
+    if (tw != 16 && tw != 32 && tw != 64) return SAR_EINVAL;
+    if (tw == pl->tile_w) return SAR_OK;
+    sar_plan::Tiling prev = pl->tilings[0];
+    for (const sar_plan::Tiling &t : pl->tilings)
+        if (t.tw == pl->tile_w) prev = t;
+    const int rg = pl->rg, minb = pl->minb, Mb0 = pl->Mb;
+    int idx = -1;
+    for (size_t i = 0; i < pl->tilings.size(); ++i)
+        if (pl->tilings[i].tw == tw) idx = (int)i;
+    if (idx < 0) {
+        HostTiles ht;
+        int64_t np = 0;
+        int rc = build_tiles(&pl->grid, ht, &np, tw);
+        if (rc) return rc;
+        const int L = window_length(pl, ht);
+        if (bp_smem_bytes(1, pl->p.n_rx, L, pl->fp16) > kBpSmemMax) return SAR_EINVAL;
+        rc = install_tiling(pl, ht, tw, L);
+        if (rc) return rc;
+        idx = (int)pl->tilings.size() - 1;
+    }
+    use_tiling(pl, pl->tilings[idx]);
+    const int Mb = default_block(pl, pl->L);
+    if (apply_launch(pl, rg, minb, Mb) == SAR_OK || apply_launch(pl, rg, 2, Mb) == SAR_OK ||
+        apply_launch(pl, default_rx_group(pl->p.n_rx), 2, Mb) == SAR_OK)
+        return SAR_OK;
+    use_tiling(pl, prev);
+    apply_launch(pl, rg, minb, Mb0);
+    return SAR_EINVAL;
+}
+
 int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t budget, sar_plan **out) {
     int rc = validate_params(params);
     if (rc) return rc;
@@ -518,30 +641,24 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
     pl->fd_max = (float)p.max_doppler_bins;
 
     HostTiles ht;
-    rc = build_tiles(grid, ht, &pl->n_pixels);
+    const int tw0 = grid->pixels_xy == nullptr ? 32 : 0;
+    rc = build_tiles(grid, ht, &pl->n_pixels, tw0);
     if (rc) {
         delete pl;
         return rc;
     }
-    pl->n_tiles = (int)ht.tiles.size();
-
-    // staged window length: covers a1 * (d0 -+ 2 rho) -+ fd_max plus guards
-    const double span = 4.0 * ht.rho_max * pl->a1 + 2.0 * std::ceil(p.max_doppler_bins);
-    int L = (int)std::ceil(span) + 2 * kGuardBins + 4;
-    L = (L + 3) & ~3;
-    pl->L = L;
-    for (TileInfo &ti : ht.tiles) {
-        const double o_allow = ((double)(L - 3 - 2 * kGuardBins) - 2.0 * pl->fd_max - 4.0 * ti.rho * pl->a1) /
-                               (2.0 * pl->a1);
-        ti.o_allow = (float)o_allow;
-        ti.klo_off = (float)(pl->a1 * (2.0 * ti.rho + o_allow) + pl->fd_max);
+    if (tw0) {
+        pl->grid = *grid;
+        pl->grid.pixels_xy = nullptr;
     }
+    pl->tile_w = tw0;
+    pl->n_tiles = (int)ht.tiles.size();
+    pl->L = window_length(pl, ht);
+    pl->key_L = pl->L;
+    pl->key_tiles = pl->n_tiles;
     pl->rg = default_rx_group(p.n_rx);
-    const size_t per_pulse = bp_smem_bytes(1, p.n_rx, L, pl->fp16);
-    int Mb = (int)std::min<size_t>(kMaxPulsesPerBlock, std::max<size_t>(1, kBpSmemTarget / per_pulse));
-    while (Mb > 1 && bp_smem_bytes(Mb, p.n_rx, L, pl->fp16) > kBpSmemTarget) --Mb;
-    pl->Mb = Mb;
-    pl->bp_smem = bp_smem_bytes(Mb, p.n_rx, L, pl->fp16);
+    pl->Mb = default_block(pl, pl->L);
+    pl->bp_smem = bp_smem_bytes(pl->Mb, p.n_rx, pl->L, pl->fp16);
     if (pl->bp_smem > kBpSmemMax) {
         delete pl;
         return SAR_EINVAL;  // reconstruction points too spread out for one tile window
@@ -568,13 +685,6 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
         return SAR_ECUDA;
     }
     pl->G = pl->num_sms * pl->ctas_per_sm;
-    // partial sums sized for any grid up to 3 CTAs per SM (the autotuner's range)
-    {
-        const int g_min = std::min(pl->G, pl->num_sms * 2), g_max = std::max(pl->G, pl->num_sms * 3);
-        pl->seg_cap = pl->n_tiles / g_min + 2;
-        pl->partial_slots = (size_t)g_max * pl->seg_cap;
-    }
-    recall_shape(pl);
 
     // FP64 tables
     std::vector<float> wr = range_window(p.range_window, p.n_samples, p.kaiser_beta);
@@ -618,14 +728,8 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
     if (!rc && pl->rc_split) rc = upload(pl, rc_twd, &pl->d_rc_twd);
     if (!rc) rc = upload(pl, tw, &pl->d_tw);
     if (!rc) rc = upload(pl, rot, &pl->d_rot);
-    if (!rc) rc = upload(pl, ht.pix, &pl->d_pix);
-    if (!rc) rc = upload(pl, ht.out, &pl->d_out);
-    if (!rc) rc = upload(pl, ht.tiles, &pl->d_tiles);
-    if (!rc) {
-        void *q = nullptr;
-        rc = dev_alloc(pl, pl->partial_slots * kTilePx * sizeof(float2), &q);
-        pl->d_partial = (float2 *)q;
-    }
+    if (!rc) rc = install_tiling(pl, ht, tw0, pl->L);
+    if (!rc) use_tiling(pl, pl->tilings.back());
     if (!rc) {
         void *q = nullptr;
         rc = dev_alloc(pl, sizeof(int) * 4, &q);
@@ -641,6 +745,7 @@ int plan_create(const sar_radar_params *params, const sar_grid *grid, size_t bud
         free_plan(pl);
         return rc;
     }
+    recall_shape(pl);
     *out = pl;
     return SAR_OK;
 }
@@ -898,6 +1003,8 @@ int sar_plan_get_info(const sar_plan *pl, sar_plan_info *info) {
     i.device_bytes = pl->used;
     i.rx_group = pl->rg;
     i.regs_ctas_per_sm = pl->minb;
+    i.tile_w = pl->tile_w;
+    i.tile_h = pl->tile_w ? kTilePx / pl->tile_w : 0;
     *info = i;
     return SAR_OK;
 }
@@ -1485,61 +1592,77 @@ int sar_plan_autotune(sar_plan *pl, const void *prof_dev, int32_t M, const doubl
     if (!dg.ok) return SAR_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
     struct Cfg {
-        int rg, minb, Mb;
+        int tw, rg, minb, Mb;
     };
-    std::vector<Cfg> cands;
-    const int R = pl->p.n_rx;
-    const int rg0 = default_rx_group(R);
-    int rg1 = 0;
-    for (int g = rg0 - 1; g >= 1 && !rg1; --g)
-        if (R % g == 0) rg1 = g;
-    const size_t budgets[2] = {kBpSmemTarget, 73 * 1024};
-    for (int rg : {rg0, rg1}) {
-        if (rg < 1) continue;
-        for (int minb = 2; minb <= 3; ++minb) {
-            int mb_max = 0;
-            for (int mb = kMaxPulsesPerBlock; mb >= 1; --mb)
-                if (bp_smem_bytes(mb, R, pl->L, pl->fp16) <= budgets[minb - 2]) {
-                    mb_max = mb;
-                    break;
-                }
-            if (mb_max == 0) continue;
-            for (int mb : {mb_max, std::max(1, (mb_max * 2) / 3), std::max(1, mb_max / 2)}) {
-                bool dup = false;
-                for (const Cfg &d : cands) dup |= (d.rg == rg && d.minb == minb && d.Mb == mb);
-                if (!dup) cands.push_back(Cfg{rg, minb, mb});
-            }
-        }
-    }
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SAR_ECUDA;
-    const Cfg saved{pl->rg, pl->minb, pl->Mb};
+    if (cudaEventCreate(&e0) != cudaSuccess) return SAR_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return SAR_ECUDA;
+    }
+    const Cfg saved{pl->tile_w, pl->rg, pl->minb, pl->Mb};
     float best = 1e30f;
     Cfg best_c = saved;
     int rc = SAR_OK;
-    for (const Cfg &c : cands) {
-        if (apply_launch(pl, c.rg, c.minb, c.Mb) != SAR_OK) continue;  // does not fit: skip
-        float times[3];
-        for (int rep = -1; rep < 3 && rc == SAR_OK; ++rep) {
-            if (rep >= 0 && cudaEventRecord(e0, s) != cudaSuccess) rc = SAR_ECUDA;
-            if (!rc) rc = bp_launch(pl, prof_dev, M, q_tx_dev, q_rx_dev, nullptr, image_dev, 0, s);
-            if (!rc && rep >= 0) {
-                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                    cudaEventElapsedTime(&times[rep], e0, e1) != cudaSuccess)
-                    rc = SAR_ECUDA;
+    // tile shapes (Cartesian grids), then per tiling the Rx group, register
+    // budget and pulse block
+    std::vector<int> tws{pl->tile_w};
+    if (pl->tile_w)
+        for (int tw : {32, 64, 16})
+            if (tw != pl->tile_w) tws.push_back(tw);
+    for (int tw : tws) {
+        if (rc) break;
+        if (tw != pl->tile_w && plan_retile(pl, tw) != SAR_OK) continue;  // does not fit: skip
+        std::vector<Cfg> cands;
+        const int R = pl->p.n_rx;
+        const int rg0 = default_rx_group(R);
+        int rg1 = 0;
+        for (int g = rg0 - 1; g >= 1 && !rg1; --g)
+            if (R % g == 0) rg1 = g;
+        const size_t budgets[2] = {kBpSmemTarget, 73 * 1024};
+        for (int rg : {rg0, rg1}) {
+            if (rg < 1) continue;
+            for (int minb = 2; minb <= 3; ++minb) {
+                int mb_max = 0;
+                for (int mb = kMaxPulsesPerBlock; mb >= 1; --mb)
+                    if (bp_smem_bytes(mb, R, pl->L, pl->fp16) <= budgets[minb - 2]) {
+                        mb_max = mb;
+                        break;
+                    }
+                if (mb_max == 0) continue;
+                for (int mb : {mb_max, std::max(1, (mb_max * 2) / 3), std::max(1, mb_max / 2)}) {
+                    bool dup = false;
+                    for (const Cfg &d : cands) dup |= (d.rg == rg && d.minb == minb && d.Mb == mb);
+                    if (!dup) cands.push_back(Cfg{tw, rg, minb, mb});
+                }
             }
         }
-        if (rc) break;
-        std::sort(times, times + 3);
-        if (times[1] < best) {
-            best = times[1];
-            best_c = c;
+        for (const Cfg &c : cands) {
+            if (apply_launch(pl, c.rg, c.minb, c.Mb) != SAR_OK) continue;  // does not fit: skip
+            float times[3];
+            for (int rep = -1; rep < 3 && rc == SAR_OK; ++rep) {
+                if (rep >= 0 && cudaEventRecord(e0, s) != cudaSuccess) rc = SAR_ECUDA;
+                if (!rc) rc = bp_launch(pl, prof_dev, M, q_tx_dev, q_rx_dev, nullptr, image_dev, 0, s);
+                if (!rc && rep >= 0) {
+                    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&times[rep], e0, e1) != cudaSuccess)
+                        rc = SAR_ECUDA;
+                }
+            }
+            if (rc) break;
+            std::sort(times, times + 3);
+            if (times[1] < best) {
+                best = times[1];
+                best_c = c;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     const Cfg fin = rc ? saved : best_c;
-    if (apply_launch(pl, fin.rg, fin.minb, fin.Mb) != SAR_OK && !rc) rc = SAR_ECUDA;
+    if ((fin.tw != pl->tile_w && plan_retile(pl, fin.tw) != SAR_OK) ||
+        apply_launch(pl, fin.rg, fin.minb, fin.Mb) != SAR_OK)
+        if (!rc) rc = SAR_ECUDA;
     if (!rc) remember_shape(pl);
     return rc;
 }
@@ -1605,6 +1728,7 @@ int sar_batch_autotune(sar_batch *b, void *stream) {
             }
         }
         b->shape[k].mb = mb_best;
+        b->shape[k].ms = t_best;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1629,6 +1753,7 @@ int sar_batch_get_class(const sar_batch *b, int32_t index, sar_batch_class *out)
     r.regs_ctas_per_sm = 2;
     r.units = c.units;
     r.updates = c.updates;
+    r.tuned_ms = b->shape[k].ms;
     *out = r;
     return SAR_OK;
 }
@@ -1638,6 +1763,17 @@ int sar_plan_set_launch(sar_plan *pl, int32_t rx_group, int32_t regs_ctas_per_sm
     DeviceGuard dg(pl->device);
     if (!dg.ok) return SAR_ECUDA;
     return apply_launch(pl, rx_group, regs_ctas_per_sm, pulses_per_block);
+}
+
+int sar_plan_set_tile_shape(sar_plan *pl, int32_t tile_w) {
+    if (!pl) return SAR_EINVAL;
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return SAR_ECUDA;
+    try {
+        return plan_retile(pl, tile_w);
+    } catch (const std::bad_alloc &) {
+        return SAR_ENOMEM;
+    }
 }
 
 int sar_plan_check_errors(sar_plan *pl) {

@@ -140,7 +140,10 @@ int main(void) {
   P(sar_radar_params, max_doppler_bins)
   P(sar_grid, pixels_xy) P(sar_grid, n_pixels)
   P(sar_plan_info, n_pixels) P(sar_plan_info, bins_per_metre) P(sar_plan_info, device_bytes)
-  P(sar_plan_info, rx_group) P(sar_plan_info, regs_ctas_per_sm)
+  P(sar_plan_info, rx_group) P(sar_plan_info, regs_ctas_per_sm) P(sar_plan_info, tile_w)
+  P(sar_plan_info, tile_h)
+  printf("sar_batch_class %zu\n", sizeof(sar_batch_class));
+  P(sar_batch_class, units) P(sar_batch_class, updates) P(sar_batch_class, tuned_ms)
   printf("sar_server_config %zu\nsar_request %zu\nsar_server_stats %zu\n",
          sizeof(sar_server_config), sizeof(sar_request), sizeof(sar_server_stats));
   P(sar_request, M) P(sar_request, w_az_host) P(sar_request, image_host)
@@ -171,6 +174,11 @@ int main(void) {
     assert int(got["sar_plan_info.device_bytes"]) == sar.PlanInfo.device_bytes.offset
     assert int(got["sar_plan_info.rx_group"]) == sar.PlanInfo.rx_group.offset
     assert int(got["sar_plan_info.regs_ctas_per_sm"]) == sar.PlanInfo.regs_ctas_per_sm.offset
+    assert int(got["sar_plan_info.tile_w"]) == sar.PlanInfo.tile_w.offset
+    assert int(got["sar_plan_info.tile_h"]) == sar.PlanInfo.tile_h.offset
+    assert int(got["sar_batch_class"]) == ctypes.sizeof(sar.BatchClass)
+    for f in ("units", "updates", "tuned_ms"):
+        assert int(got[f"sar_batch_class.{f}"]) == getattr(sar.BatchClass, f).offset
     assert int(got["sar_server_config"]) == ctypes.sizeof(sar.ServerConfig)
     assert int(got["sar_request"]) == ctypes.sizeof(sar.RequestDesc)
     assert int(got["sar_server_stats"]) == ctypes.sizeof(sar.ServerStats)

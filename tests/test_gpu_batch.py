@@ -25,9 +25,9 @@ def _single(r):
 
 
 def test_mixed_batch_equals_single_requests():
-    """Requests with different plans, Rx counts, storages, sizes and point
-    lists: each batched image equals its own sar_backproject image (same sum
-    up to FP32 ordering) and the oracle."""
+    """Requests with different plans, Rx counts, storages, sizes, tile shapes
+    and point lists: each batched image equals its own sar_backproject image
+    (same sum up to FP32 ordering) and the oracle."""
     import torch
     import paper_2306_09784_gb300 as sar
     reqs = []
@@ -37,6 +37,9 @@ def test_mixed_batch_equals_single_requests():
     for wl in synth.make_batched_requests(5, seed=11, m_range=(40, 200), side_range=(32, 160),
                                           n_samples=128):
         reqs.append(_prepare(wl, precision=int(wl.radar.n_rx % 2)))
+    # plans on other tile shapes mix with the default ones
+    reqs[0]["plan"].set_tile_shape(64)
+    reqs[3]["plan"].set_tile_shape(16)
     batch = sar.Batch(len(reqs))
     images = []
     for r in reqs:
