@@ -53,7 +53,7 @@ MUFU_LANES = 16
 # backprojection launch on this workload, from an ncu --set full capture of
 # the kernel source with this SHA-256 prefix (reported as null once the
 # kernel source differs).
-BP_TRAFFIC = {"sha256_16": "782954157b053083", "bytes": 33887488 + 5376}
+BP_TRAFFIC = {"sha256_16": "0d40cefaa5ecc9c3", "bytes": 33770752 + 23808}
 HBM_PEAK_FALLBACK_GBS = 6800.0
 
 
@@ -430,7 +430,13 @@ def bench_batched(dev, stream, reps=5, n_req=64, seed=5):
     errs = [float((r["img_batch"] - r["img_plain"]).abs().norm() / r["img_plain"].abs().norm())
             for r in reqs]
     _, units, ctas = batch.info()
-    return {"requests": len(reqs), "updates": upd,
+    for c in classes:
+        c["gupdates_per_s"] = c["updates"] / (c["tuned_ms"] * 1e6) if c["tuned_ms"] > 0 else None
+    tiles = {}
+    for r in reqs:
+        t = "x".join(str(v) for v in r["plan"].launch_shape()["tile"])
+        tiles[t] = tiles.get(t, 0) + 1
+    return {"requests": len(reqs), "updates": upd, "plan_tiles": tiles,
             "plain_frames_per_s": len(reqs) / t_plain, "batched_frames_per_s": len(reqs) / t_batch,
             "plain_ms": t_plain * 1e3, "batched_ms": t_batch * 1e3,
             "speedup": t_plain / t_batch, "batched_gupdates_per_s": upd / t_batch / 1e9,
