@@ -1365,7 +1365,12 @@ int sar_batch_commit(sar_batch *b, void *stream) {
         const int k = (c.fp16 ? 4 : 0) + c.rg - 1;
         if (b->occ_smem[k] != c.smem || b->occ_ctas[k] < 1) {
             int occ = 0;
-            if (bp_batch_prepare(c.rg, c.fp16, c.smem, &occ) != cudaSuccess || occ < 1) {
+            const cudaError_t e = bp_batch_prepare(c.rg, c.fp16, c.smem, &occ);
+            if (e == cudaErrorInvalidValue) {  // the class's shared memory exceeds what a CTA can have
+                cudaGetLastError();
+                return SAR_EINVAL;
+            }
+            if (e != cudaSuccess || occ < 1) {
                 cudaGetLastError();
                 return SAR_ECUDA;
             }

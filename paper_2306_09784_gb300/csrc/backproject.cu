@@ -320,15 +320,19 @@ __device__ __forceinline__ void stage_block(const BpArgs &a, const Smem &sm, int
     const uint32_t raw = sm.base_addr + sm.lay.raw;
     const int n_items = np * R * nq;
     const long long row0 = (long long)b * MbR;  // window w reads profile row row0 + w
+    // loop invariants as locals: the copies' asm statements clobber memory,
+    // which would otherwise reload them every item
+    const unsigned long long div_nq = a.div_nq, div_r = a.div_r;
+    const int n_bins = a.n_bins, crop_lo = a.crop_lo, crop_hi = a.crop_hi;
     for (int it = threadIdx.x; it < n_items; it += blockDim.x) {
-        const int w = fast_div(it, a.div_nq);
+        const int w = fast_div(it, div_nq);
         const int q = it - w * nq;
-        const int p = exact ? 0 : fast_div(w, a.div_r);
+        const int p = exact ? 0 : fast_div(w, div_r);
         const int k0 = window_start(sm, cslot, Mb, MbR, w, p, exact) + 4 * q;
         // sample k of this row sits at prof + (base + k) * SB
-        const long long base = (row0 + w) * a.n_bins - a.crop_lo;
+        const long long base = (row0 + w) * n_bins - crop_lo;
         const uint32_t dst = raw + (uint32_t)it * 5u * SB;
-        if (k0 >= a.crop_lo && k0 + 4 <= a.crop_hi) {
+        if (k0 >= crop_lo && k0 + 4 <= crop_hi) {
             const unsigned char *src = prof + (base + k0) * SB;
 #pragma unroll
             for (int e = 0; e < 5; ++e) cp_async<SB>(dst + e * SB, src + e * SB, SB);
@@ -336,8 +340,8 @@ __device__ __forceinline__ void stage_block(const BpArgs &a, const Smem &sm, int
 #pragma unroll
             for (int e = 0; e < 5; ++e) {
                 const int k = k0 + e;
-                const bool ok = (k >= a.crop_lo) && (k <= a.crop_hi);
-                const void *src = ok ? (const void *)(prof + (base + k) * SB) : a.prof;
+                const bool ok = (k >= crop_lo) && (k <= crop_hi);
+                const void *src = ok ? (const void *)(prof + (base + k) * SB) : (const void *)prof;
                 cp_async<SB>(dst + e * SB, src, ok ? SB : 0);
             }
         }
@@ -356,13 +360,18 @@ __device__ __forceinline__ void convert_block(const BpArgs &a, const Smem &sm, i
     const int np = min(Mb, a.M - b * Mb);
     const int nq = a.L >> 2;
     const int4 *pr = sm.pair(cslot, MbR);
-    float4 *table = sm.table(tslot, MbR * a.L);
+    const int L = a.L;
+    float4 *table = sm.table(tslot, MbR * L);
     const unsigned char *raw = sm.base + sm.lay.raw;
     const int n_items = np * R * nq;
+    const unsigned long long div_nq = a.div_nq, div_r = a.div_r;
+    const int crop_lo = a.crop_lo, crop_hi = a.crop_hi;
+    const float2 cbk = a.cb_k;
+    const float ik = a.inv_kappa;
     for (int it = threadIdx.x; it < n_items; it += blockDim.x) {
-        const int w = fast_div(it, a.div_nq);
+        const int w = fast_div(it, div_nq);
         const int q = it - w * nq;
-        const int p = exact ? 0 : fast_div(w, a.div_r);
+        const int p = exact ? 0 : fast_div(w, div_r);
         const int k0 = window_start(sm, cslot, Mb, MbR, w, p, exact) + 4 * q;
         float2 s[5];
         if (FP16) {
@@ -378,14 +387,12 @@ __device__ __forceinline__ void convert_block(const BpArgs &a, const Smem &sm, i
 #pragma unroll
             for (int e = 0; e < 5; ++e) s[e] = f[e];
         }
-        float4 *dst = table + w * a.L + 4 * q;
-        const float2 cbk = a.cb_k;
-        const float ik = a.inv_kappa;
-        const bool inside = k0 >= a.crop_lo && k0 + 3 < a.crop_hi;
+        float4 *dst = table + w * L + 4 * q;
+        const bool inside = k0 >= crop_lo && k0 + 3 < crop_hi;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int k = k0 + e;
-            const bool valid = inside || ((k >= a.crop_lo) && (k < a.crop_hi));
+            const bool valid = inside || ((k >= crop_lo) && (k < crop_hi));
             const float dre = fmaf(s[e + 1].x, cbk.x, fmaf(-s[e + 1].y, cbk.y, -s[e].x * ik));
             const float dim = fmaf(s[e + 1].x, cbk.y, fmaf(s[e + 1].y, cbk.x, -s[e].y * ik));
             const float4 ent = make_float4(s[e].x, s[e].y, dre, dim);
@@ -783,6 +790,10 @@ __device__ __forceinline__ void run_class(const BpCheck &M, const BpClassArgs &B
             batch_fail(M.err, 2, u, j, B.n_jobs);
             return;
         }
+        // a private copy of the job's arguments (a few bytes of it spill).
+        // Read in place instead, every field access after a copy's or load's
+        // memory clobber becomes a load: from a shared-memory copy 2-11 %
+        // slower per class, through a restricted global reference 3-10 %.
         const BpArgs a = B.jobs[j];
         sm.lay = bp_layout(a.Mb, a.R, a.L, FP16);
         if (!(a.Mb >= 1 && a.Mb <= 32 && sm.lay.total <= M.smem_bytes && a.R == B.rg * (a.R / B.rg) &&
@@ -942,8 +953,19 @@ size_t bp_smem_bytes(int Mb, int R, int L, bool fp16) { return bp_layout(Mb, R, 
 
 // The dynamic shared-memory limit is a per-kernel, process-wide attribute:
 // plans (and batches) of different sizes share the kernels, so it is raised
-// once to the largest size any of them may use, never lowered.
+// once to the largest size any of them may use, never lowered: 227 KB less
+// the kernel's static shared memory.
 constexpr int kSmemLimit = 227 * 1024;
+
+// Raise kernel k's dynamic shared-memory limit; *max_dyn receives it.
+cudaError_t raise_smem_limit(const void *k, size_t *max_dyn) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k);
+    if (e != cudaSuccess) return e;
+    if (fa.sharedSizeBytes >= (size_t)kSmemLimit) return cudaErrorInvalidValue;
+    *max_dyn = (size_t)kSmemLimit - fa.sharedSizeBytes;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*max_dyn);
+}
 
 cudaError_t bp_prepare(bool fp16, int rg, size_t smem) {
     if (smem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
@@ -951,8 +973,10 @@ cudaError_t bp_prepare(bool fp16, int rg, size_t smem) {
         for (int minb = 2; minb <= 3; ++minb) {
             void *k = select_kernel(rg, fp16, fd != 0, minb);
             if (!k) return cudaErrorInvalidValue;
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+            size_t max_dyn = 0;
+            cudaError_t e = raise_smem_limit(k, &max_dyn);
             if (e != cudaSuccess) return e;
+            if (smem > max_dyn) return cudaErrorInvalidValue;
         }
     return cudaSuccess;
 }
@@ -984,8 +1008,10 @@ void *select_class_kernel(int rg, bool fp16) {
 cudaError_t bp_batch_prepare(int rg, bool fp16, size_t smem, int *ctas_per_sm) {
     void *k = select_class_kernel(rg, fp16);
     if (!k || smem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    size_t max_dyn = 0;
+    cudaError_t e = raise_smem_limit(k, &max_dyn);
     if (e != cudaSuccess) return e;
+    if (smem > max_dyn) return cudaErrorInvalidValue;
 
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k, kBpThreads, smem);
 }
