@@ -331,11 +331,14 @@ int sar_backproject_noalloc(sar_plan *plan, const void *prof_dev, int32_t M,
  *
  * Use: sar_batch_clear, sar_batch_add per request, sar_batch_commit (groups
  * the requests by class and uploads the request table on `stream`), then
- * sar_batch_launch (one kernel per class and the fix-up on `stream`, reading
- * only device memory: it can be captured in a CUDA graph and replayed while
- * the table and the request buffers stay unchanged).  sar_batch_autotune
- * picks each class's pulse block.  All plans of a batch must be on the
- * batch's device; the batch owns its request table (pinned host + device) and
+ * sar_batch_launch (one kernel per class and the fix-up on `stream`; a class
+ * of up to 128 requests gets their kernel arguments as launch parameters,
+ * larger ones read the uploaded table; it can be captured in a CUDA graph,
+ * which keeps the parameters of the committed batch, and replayed while the
+ * batch is not committed again and the request buffers stay unchanged).
+ * sar_batch_autotune picks each class's pulse block and argument source.
+ * All plans of a batch must be on the batch's device; the batch owns its
+ * request table (pinned host + device) and
  * partial sums of 16 KB per CTA and class (39 MB on 152 SMs).
  * Requests of one batch must not write the same image.
  */
@@ -377,7 +380,10 @@ int sar_batch_get_info(const sar_batch *batch, int32_t *n_jobs, int64_t *units, 
  * Autotuner of the batched launch (no counterpart in the paper): it times
  * every class's launch with chirps per pipeline block from {each request's
  * plan's own, the largest that fits two CTAs per SM for every request of the
- * class, 2/3 and 1/2 of that} and keeps each class's fastest.  Needs a
+ * class, 2/3 and 1/2 of that} and keeps each class's fastest; at that block
+ * it then times a class of up to 128 requests with its arguments read from
+ * the device table instead of passed as launch parameters, and keeps the
+ * faster source (the two give identical images).  Needs a
  * committed batch; re-commits it on `stream` and blocks until the timing runs
  * finish.  The requests' images are overwritten (and accumulating requests
  * accumulate repeatedly): their contents are undefined afterwards.  The
@@ -397,6 +403,10 @@ typedef struct sar_batch_class {
     double updates;            /* pixel slots x chirps x Rx */
     double tuned_ms;           /* the class launch (with its fix-up) at the chosen block, as timed by
                                   sar_batch_autotune; 0 before it runs */
+    int32_t param_args;        /* 1: the requests' kernel arguments travel as launch parameters (classes
+                                  of up to 128 requests), 0: the kernel reads them from the batch's
+                                  device table */
+    int32_t reserved;
 } sar_batch_class;
 
 int sar_batch_num_classes(const sar_batch *batch, int32_t *n_classes);

@@ -85,7 +85,8 @@ class BatchClass(ctypes.Structure):
     _fields_ = [("rx_group", ctypes.c_int32), ("fp16", ctypes.c_int32), ("n_jobs", ctypes.c_int32),
                 ("pulses_per_block", ctypes.c_int32), ("ctas", ctypes.c_int32),
                 ("regs_ctas_per_sm", ctypes.c_int32), ("units", ctypes.c_int64),
-                ("updates", ctypes.c_double), ("tuned_ms", ctypes.c_double)]
+                ("updates", ctypes.c_double), ("tuned_ms", ctypes.c_double),
+                ("param_args", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):

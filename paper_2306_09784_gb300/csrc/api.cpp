@@ -100,7 +100,8 @@ struct BatchClass {
 // (0 = each request's plan's own).
 struct ClassShape {
     int mb = 0;
-    float ms = 0.f;  // its launch time as measured by sar_batch_autotune (0: not tuned)
+    bool param = true;  // job arguments as kernel parameters (classes of up to kParamJobs requests)
+    float ms = 0.f;     // its launch time as measured by sar_batch_autotune (0: not tuned)
 };
 
 struct sar_batch {
@@ -1475,7 +1476,9 @@ int batch_launch_class(const sar_batch *b, int ci, cudaStream_t s) {
     m.cls[0].tile_base = 0;
     m.n_classes = 1;
     const BpCheck chk = batch_check(b, c.smem);
-    if (launch_backproject_class(a, chk, c.smem, s) != cudaSuccess) return SAR_ECUDA;
+    const int k = (c.fp16 ? 4 : 0) + c.rg - 1;
+    const BpArgs *host_jobs = b->shape[k].param ? b->h_sorted + c.j0 : nullptr;
+    if (launch_backproject_class(a, chk, c.smem, s, host_jobs) != cudaSuccess) return SAR_ECUDA;
     return launch_batch_fixup(m, chk, c.tiles, s) == cudaSuccess ? SAR_OK : SAR_ECUDA;
 }
 
@@ -1505,7 +1508,9 @@ int sar_batch_launch(sar_batch *b, void *stream) {
     for (int ci = 0; ci < b->n_classes; ++ci) {
         m.cls[ci] = class_args(b, ci, 0, b->cls[ci].cta_begin);
         smem_max = std::max(smem_max, b->cls[ci].smem);
-        if (launch_backproject_class(m.cls[ci], batch_check(b, b->cls[ci].smem), b->cls[ci].smem, s) !=
+        const int k = (b->cls[ci].fp16 ? 4 : 0) + b->cls[ci].rg - 1;
+        const BpArgs *host_jobs = b->shape[k].param ? b->h_sorted + b->cls[ci].j0 : nullptr;
+        if (launch_backproject_class(m.cls[ci], batch_check(b, b->cls[ci].smem), b->cls[ci].smem, s, host_jobs) !=
             cudaSuccess)
             return SAR_ECUDA;
     }
@@ -1733,6 +1738,18 @@ int sar_batch_autotune(sar_batch *b, void *stream) {
             }
         }
         b->shape[k].mb = mb_best;
+        // then the job arguments' source at that block: kernel parameters
+        // (the default) or the device table
+        if (rc == SAR_OK && c0.n <= kParamJobs) {
+            b->shape[k].param = false;
+            rc = sar_batch_commit(b, stream);
+            float t = 0;
+            if (rc == SAR_OK) time_class(ci, &t);
+            if (rc == SAR_OK && t < t_best)
+                t_best = t;
+            else
+                b->shape[k].param = true;
+        }
         b->shape[k].ms = t_best;
     }
     cudaEventDestroy(e0);
@@ -1759,6 +1776,7 @@ int sar_batch_get_class(const sar_batch *b, int32_t index, sar_batch_class *out)
     r.units = c.units;
     r.updates = c.updates;
     r.tuned_ms = b->shape[k].ms;
+    r.param_args = (b->shape[k].param && c.n <= kParamJobs) ? 1 : 0;
     *out = r;
     return SAR_OK;
 }

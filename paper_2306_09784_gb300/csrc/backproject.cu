@@ -42,6 +42,9 @@
 //    reduces the per-block loop choice.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <cstring>
+
 #include "sar_internal.h"
 
 namespace sar {
@@ -764,13 +767,16 @@ __device__ __forceinline__ void batch_fail(int *err, int code, long long x, long
     }
 }
 
-template <int RG, bool FP16>
-__device__ __forceinline__ void run_class(const BpCheck &M, const BpClassArgs &B, int cta, float2 *scratch,
-                                          uint32_t smem_addr, unsigned char *smem_base) {
+// PARAM: `jobs` points into the kernel's parameter table (read in place from
+// the constant bank, as a single request's arguments are); otherwise at the
+// device table (each segment takes a private copy).
+template <int RG, bool FP16, bool PARAM>
+__device__ __forceinline__ void run_class(const BpCheck &M, const BpClassArgs &B, const BpArgs *jobs, int cta,
+                                          float2 *scratch, uint32_t smem_addr, unsigned char *smem_base) {
     Smem sm;
     sm.base = smem_base;
     sm.base_addr = smem_addr;
-    if (!(cta >= 0 && cta < B.G && B.units > 0 && B.n_jobs > 0)) {
+    if (!(cta >= 0 && cta < B.G && B.units > 0 && B.n_jobs > 0 && (!PARAM || B.n_jobs <= kParamJobs))) {
         batch_fail(M.err, 1, cta, B.G, B.units);
         return;
     }
@@ -784,22 +790,14 @@ __device__ __forceinline__ void run_class(const BpCheck &M, const BpClassArgs &B
     }
     int j = lo;
     long long u = u0;
-    while (u < u1) {
-        while (j + 1 < B.n_jobs && u >= B.unit_begin[j + 1]) ++j;
-        if (!(u >= B.unit_begin[j] && u < B.unit_begin[j + 1])) {
-            batch_fail(M.err, 2, u, j, B.n_jobs);
-            return;
-        }
-        // a private copy of the job's arguments (a few bytes of it spill).
-        // Read in place instead, every field access after a copy's or load's
-        // memory clobber becomes a load: from a shared-memory copy 2-11 %
-        // slower per class, through a restricted global reference 3-10 %.
-        const BpArgs a = B.jobs[j];
+    // units [u, ...) of job j with arguments a: one segment; returns the units
+    // processed, -1 after a failed check
+    auto segment = [&](const BpArgs &a) -> long long {
         sm.lay = bp_layout(a.Mb, a.R, a.L, FP16);
         if (!(a.Mb >= 1 && a.Mb <= 32 && sm.lay.total <= M.smem_bytes && a.R == B.rg * (a.R / B.rg) &&
               a.fp16 == (FP16 ? 1 : 0))) {
             batch_fail(M.err, 3, a.Mb, sm.lay.total, M.smem_bytes);
-            return;
+            return -1;
         }
         const long long v = u - B.unit_begin[j];
         const int PB = a.blocks_per_tile;
@@ -808,18 +806,39 @@ __device__ __forceinline__ void run_class(const BpCheck &M, const BpClassArgs &B
         const int b1 = (int)min((long long)PB, (long long)b0 + (u1 - u));
         if (!(PB == (a.M + a.Mb - 1) / a.Mb && tile >= 0 && tile < a.n_tiles && b0 >= 0 && b0 < b1 && b1 <= PB)) {
             batch_fail(M.err, 4, tile, b0, b1);
-            return;
+            return -1;
         }
         float2 *dst = nullptr;
         if (!(b0 == 0 && b1 == PB)) {
             if (!((long long)(B.cta_begin + cta) * 2 + 1 < M.scratch_slots)) {
                 batch_fail(M.err, 5, B.cta_begin + cta, M.scratch_slots, 0);
-                return;
+                return -1;
             }
             dst = scratch + (u == u0 ? 0 : kTilePx);
         }
         process_segment<RG, FP16, false>(a, sm, tile, b0, b1, dst);
-        u += b1 - b0;
+        return (long long)(b1 - b0);
+    };
+    while (u < u1) {
+        while (j + 1 < B.n_jobs && u >= B.unit_begin[j + 1]) ++j;
+        if (!(u >= B.unit_begin[j] && u < B.unit_begin[j + 1])) {
+            batch_fail(M.err, 2, u, j, B.n_jobs);
+            return;
+        }
+        long long done;
+        if constexpr (PARAM) {
+            done = segment(jobs[j]);
+        } else {
+            // a private copy of the job's arguments (a few bytes of it spill).
+            // Read in place from global or shared memory instead, every field
+            // access after a copy's or load's memory clobber becomes a load:
+            // 3-10 % slower per class through a restricted global reference,
+            // 2-11 % from a shared-memory copy.
+            const BpArgs a = jobs[j];
+            done = segment(a);
+        }
+        if (done < 0) return;
+        u += done;
     }
 }
 
@@ -831,7 +850,17 @@ __global__ void __launch_bounds__(kBpThreads, 2) backproject_class_kernel(BpClas
     extern __shared__ __align__(16) unsigned char smem_bp[];
     const uint32_t smem_addr = (uint32_t)__cvta_generic_to_shared(smem_bp);
     float2 *scratch = chk.scratch + ((long long)B.cta_begin + blockIdx.x) * 2 * kTilePx;
-    run_class<RG, FP16>(chk, B, (int)blockIdx.x, scratch, smem_addr, smem_bp);
+    run_class<RG, FP16, false>(chk, B, B.jobs, (int)blockIdx.x, scratch, smem_addr, smem_bp);
+}
+
+// The same with the class's jobs (at most kParamJobs) as a kernel parameter.
+template <int RG, bool FP16>
+__global__ void __launch_bounds__(kBpThreads, 2)
+    backproject_class_param_kernel(BpClassArgs B, BpCheck chk, const __grid_constant__ BpJobTable T) {
+    extern __shared__ __align__(16) unsigned char smem_bp[];
+    const uint32_t smem_addr = (uint32_t)__cvta_generic_to_shared(smem_bp);
+    float2 *scratch = chk.scratch + ((long long)B.cta_begin + blockIdx.x) * 2 * kTilePx;
+    run_class<RG, FP16, true>(chk, B, T.jobs, (int)blockIdx.x, scratch, smem_addr, smem_bp);
 }
 
 // Fix-up of the batched form: one CTA per tile of every request of every
@@ -992,9 +1021,15 @@ int bp_occupancy(bool fp16, int rg, size_t smem, int minb, int *ctas_per_sm) {
 
 namespace {
 
-void *select_class_kernel(int rg, bool fp16) {
-#define SAR_SELB(RGV)                                                                                     \
-    if (rg == RGV) return fp16 ? (void *)backproject_class_kernel<RGV, true> : (void *)backproject_class_kernel<RGV, false>;
+void *select_class_kernel(int rg, bool fp16, bool param) {
+#define SAR_SELB(RGV)                                                                      \
+    if (rg == RGV) {                                                                       \
+        if (param)                                                                         \
+            return fp16 ? (void *)backproject_class_param_kernel<RGV, true>                \
+                        : (void *)backproject_class_param_kernel<RGV, false>;              \
+        return fp16 ? (void *)backproject_class_kernel<RGV, true>                          \
+                    : (void *)backproject_class_kernel<RGV, false>;                        \
+    }
     SAR_SELB(1)
     SAR_SELB(2)
     SAR_SELB(3)
@@ -1005,24 +1040,44 @@ void *select_class_kernel(int rg, bool fp16) {
 
 }  // namespace
 
+// Both variants of the class kernel (job arguments from the device table or
+// from the parameters); the occupancy reported is the lower of the two.
 cudaError_t bp_batch_prepare(int rg, bool fp16, size_t smem, int *ctas_per_sm) {
-    void *k = select_class_kernel(rg, fp16);
-    if (!k || smem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
-    size_t max_dyn = 0;
-    cudaError_t e = raise_smem_limit(k, &max_dyn);
-    if (e != cudaSuccess) return e;
-    if (smem > max_dyn) return cudaErrorInvalidValue;
-
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k, kBpThreads, smem);
+    if (smem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
+    int occ = 1 << 30;
+    for (int param = 0; param < 2; ++param) {
+        void *k = select_class_kernel(rg, fp16, param != 0);
+        if (!k) return cudaErrorInvalidValue;
+        size_t max_dyn = 0;
+        cudaError_t e = raise_smem_limit(k, &max_dyn);
+        if (e != cudaSuccess) return e;
+        if (smem > max_dyn) return cudaErrorInvalidValue;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kBpThreads, smem);
+        if (e != cudaSuccess) return e;
+        occ = std::min(occ, n);
+    }
+    *ctas_per_sm = occ;
+    return cudaSuccess;
 }
 
-cudaError_t launch_backproject_class(const BpClassArgs &c, const BpCheck &chk, size_t smem, cudaStream_t s) {
+cudaError_t launch_backproject_class(const BpClassArgs &c, const BpCheck &chk, size_t smem, cudaStream_t s,
+                                     const BpArgs *host_jobs) {
     if (c.G == 0 || c.units == 0) return cudaSuccess;
-    void *k = select_class_kernel(c.rg, c.fp16 != 0);
+    const bool param = host_jobs != nullptr && c.n_jobs >= 1 && c.n_jobs <= kParamJobs;
+    void *k = select_class_kernel(c.rg, c.fp16 != 0, param);
     if (!k) return cudaErrorInvalidValue;
     BpClassArgs a = c;
     BpCheck b = chk;
-    void *params[] = {&a, &b};
+    if (!param) {
+        void *params[] = {&a, &b};
+        return cudaLaunchKernel(k, dim3(c.G), dim3(kBpThreads), params, smem, s);
+    }
+    // the parameter block is copied at launch (and into a captured graph)
+    static thread_local BpJobTable table;
+    std::memset(&table, 0, sizeof(table));
+    std::memcpy(table.jobs, host_jobs, sizeof(BpArgs) * (size_t)c.n_jobs);
+    void *params[] = {&a, &b, &table};
     return cudaLaunchKernel(k, dim3(c.G), dim3(kBpThreads), params, smem, s);
 }
 

@@ -142,6 +142,14 @@ struct BpClassArgs {
     int fp16;                    // profile storage
 };
 constexpr int kBatchClasses = 8;  // Rx group 1..4 x storage
+// Classes of up to kParamJobs requests get their job arguments as a kernel
+// parameter (constant bank, like a single request's); larger ones read the
+// device table.
+constexpr int kParamJobs = 128;
+struct BpJobTable {
+    BpArgs jobs[kParamJobs];
+};
+static_assert(sizeof(BpJobTable) + sizeof(BpClassArgs) + 64 <= 32764, "kernel parameter limit");
 struct BpMultiArgs {
     BpClassArgs cls[kBatchClasses];
     int n_classes;
@@ -166,7 +174,10 @@ cudaError_t bp_prepare(bool fp16, int rg, size_t smem);  // sets function attrib
 int bp_occupancy(bool fp16, int rg, size_t smem, int minb, int *ctas_per_sm);
 cudaError_t launch_backproject(const BpArgs &a, const BpLaunch &l, cudaStream_t s);
 cudaError_t bp_batch_prepare(int rg, bool fp16, size_t smem, int *ctas_per_sm);
-cudaError_t launch_backproject_class(const BpClassArgs &c, const BpCheck &chk, size_t smem, cudaStream_t s);
+// host_jobs: the class's jobs in host memory (the same as c.jobs), passed as
+// parameters when there are at most kParamJobs; null to read c.jobs.
+cudaError_t launch_backproject_class(const BpClassArgs &c, const BpCheck &chk, size_t smem, cudaStream_t s,
+                                     const BpArgs *host_jobs);
 cudaError_t launch_batch_fixup(const BpMultiArgs &m, const BpCheck &chk, int total_tiles, cudaStream_t s);
 
 // Per-pixel Doppler offsets (doppler.cu).

@@ -144,6 +144,7 @@ int main(void) {
   P(sar_plan_info, tile_h)
   printf("sar_batch_class %zu\n", sizeof(sar_batch_class));
   P(sar_batch_class, units) P(sar_batch_class, updates) P(sar_batch_class, tuned_ms)
+  P(sar_batch_class, param_args)
   printf("sar_server_config %zu\nsar_request %zu\nsar_server_stats %zu\n",
          sizeof(sar_server_config), sizeof(sar_request), sizeof(sar_server_stats));
   P(sar_request, M) P(sar_request, w_az_host) P(sar_request, image_host)
@@ -177,7 +178,7 @@ int main(void) {
     assert int(got["sar_plan_info.tile_w"]) == sar.PlanInfo.tile_w.offset
     assert int(got["sar_plan_info.tile_h"]) == sar.PlanInfo.tile_h.offset
     assert int(got["sar_batch_class"]) == ctypes.sizeof(sar.BatchClass)
-    for f in ("units", "updates", "tuned_ms"):
+    for f in ("units", "updates", "tuned_ms", "param_args"):
         assert int(got[f"sar_batch_class.{f}"]) == getattr(sar.BatchClass, f).offset
     assert int(got["sar_server_config"]) == ctypes.sizeof(sar.ServerConfig)
     assert int(got["sar_request"]) == ctypes.sizeof(sar.RequestDesc)

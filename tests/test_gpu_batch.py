@@ -117,6 +117,7 @@ def test_batched_config_64_requests_graph():
     assert sum(c["units"] for c in classes) == units
     assert len({c["regs_ctas_per_sm"] for c in classes}) == 1
     assert all(c["fp16"] == 1 and c["ctas"] >= 1 and 0 <= c["pulses_per_block"] <= 32 for c in classes)
+    assert all(c["tuned_ms"] > 0 and c["param_args"] in (0, 1) for c in classes)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
         batch.launch(stream)
@@ -206,3 +207,33 @@ def test_batch_frames_range_compressed_in_packed_launches():
         single = _single(r)
         torch.cuda.synchronize()
         assert rel_l2(img.cpu().numpy(), single.cpu().numpy()) < 1e-5, r["wl"].name
+
+
+def test_batch_class_beyond_parameter_table():
+    """130 requests in one class (more than the 128 whose arguments travel as
+    launch parameters): the class kernel reads the device table; every image
+    equals the single request's, and a 2-request batch of the same plan takes
+    the parameter path with the same images."""
+    import torch
+    import paper_2306_09784_gb300 as sar
+    r = _prepare(synth.make_workload("small"), 0)
+    single = _single(r)
+    torch.cuda.synchronize()
+    for n, param in ((130, 0), (2, 1)):
+        batch = sar.Batch(n)
+        images = []
+        for _ in range(n):
+            img = torch.full((r["plan"].n_pixels,), float("nan"), dtype=torch.complex64, device="cuda")
+            batch.add(r["plan"], r["prof"], r["wl"].n_pulses, r["qt"], r["qr"], img)
+            images.append(img)
+        batch.commit()
+        batch.launch()
+        torch.cuda.synchronize()
+        assert batch.check_errors() == (sar.SAR_OK, [0, 0, 0, 0])
+        cls = batch.classes()
+        assert len(cls) == 1 and cls[0]["n_jobs"] == n and cls[0]["param_args"] == param
+        ref = single.cpu().numpy()
+        for img in images:
+            e = rel_l2(img.cpu().numpy(), ref)
+            assert e < 1e-5, (n, e)
+
