@@ -50,10 +50,10 @@ MUFU_LANES = 16
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# backprojection launch on this workload, from an ncu --set full capture of
-# the kernel source with this SHA-256 prefix (reported as null once the
-# kernel source differs).
-BP_TRAFFIC = {"sha256_16": "0d40cefaa5ecc9c3", "bytes": 33770752 + 23808}
+# backprojection launch on this workload, from an ncu capture of the kernel
+# source with this SHA-256 prefix (reported as null once the kernel source
+# differs).
+BP_TRAFFIC = {"sha256_16": "c349ed253e1a87fd", "bytes": 32666112 + 4608}
 HBM_PEAK_FALLBACK_GBS = 6800.0
 
 
