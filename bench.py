@@ -432,11 +432,14 @@ def bench_batched(dev, stream, reps=5, n_req=64, seed=5):
     _, units, ctas = batch.info()
     for c in classes:
         c["gupdates_per_s"] = c["updates"] / (c["tuned_ms"] * 1e6) if c["tuned_ms"] > 0 else None
-    tiles = {}
+    tiles, budgets = {}, {}
     for r in reqs:
-        t = "x".join(str(v) for v in r["plan"].launch_shape()["tile"])
+        sh = r["plan"].launch_shape()
+        t = "x".join(str(v) for v in sh["tile"])
         tiles[t] = tiles.get(t, 0) + 1
+        budgets[str(sh["regs_ctas_per_sm"])] = budgets.get(str(sh["regs_ctas_per_sm"]), 0) + 1
     return {"requests": len(reqs), "updates": upd, "plan_tiles": tiles,
+            "plan_regs_ctas_per_sm": budgets,
             "plain_frames_per_s": len(reqs) / t_plain, "batched_frames_per_s": len(reqs) / t_batch,
             "plain_ms": t_plain * 1e3, "batched_ms": t_batch * 1e3,
             "speedup": t_plain / t_batch, "batched_gupdates_per_s": upd / t_batch / 1e9,
