@@ -529,7 +529,9 @@ int sar_form_image_host(sar_plan *plan, const void *beat_host, int32_t M,
  * and the next smaller divisor of n_rx; CTAs per SM the registers are sized
  * for: 2 or 3; chirps per pipeline block: the largest that fits that many
  * CTAs' shared memory, 2/3 and 1/2 of it) and keeps the fastest in the plan
- * (see sar_plan_get_info).  The choice is also remembered for the process,
+ * (see sar_plan_get_info); another tile shape than the plan's current one is
+ * taken only if it is at least 2 % faster (its longer staged windows also
+ * size the pulse block of any batch class the plan joins).  The choice is also remembered for the process,
  * keyed by device, Rx count, the staged window length and tile count of the
  * plan's first tiling (tile count and max_pulses rounded up to powers of
  * two) and profile storage: plans created later with the same key start

@@ -1611,8 +1611,14 @@ int sar_plan_autotune(sar_plan *pl, const void *prof_dev, int32_t M, const doubl
         return SAR_ECUDA;
     }
     const Cfg saved{pl->tile_w, pl->rg, pl->minb, pl->Mb};
-    float best = 1e30f;
-    Cfg best_c = saved;
+    // best per tiling: the plan's tiling on entry (square tiles unless the
+    // caller chose another) and the others; another tiling must be faster by
+    // 2 % to be taken
+    // (its longer staged windows cost every batch the plan joins: a batch
+    // class sizes its pulse block for the longest window of its requests)
+    constexpr float kTileMargin = 0.98f;
+    float best = 1e30f, best_other = 1e30f;
+    Cfg best_c = saved, best_other_c = saved;
     int rc = SAR_OK;
     // tile shapes (Cartesian grids), then per tiling the Rx group, register
     // budget and pulse block
@@ -1661,12 +1667,14 @@ int sar_plan_autotune(sar_plan *pl, const void *prof_dev, int32_t M, const doubl
             }
             if (rc) break;
             std::sort(times, times + 3);
-            if (times[1] < best) {
-                best = times[1];
-                best_c = c;
+            float &b = (c.tw == tws[0]) ? best : best_other;
+            if (times[1] < b) {
+                b = times[1];
+                (c.tw == tws[0] ? best_c : best_other_c) = c;
             }
         }
     }
+    if (best_other < kTileMargin * best) best_c = best_other_c;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     const Cfg fin = rc ? saved : best_c;
