@@ -15,12 +15,15 @@ from tests.gpu_helpers import TOL_FP32, make_plan, oracle_image, rel_l2, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def _frame(wl, precision=0):
-    """Host (pinned) inputs of one frame, its plan and its stand-alone image."""
+def _frame(wl, precision=0, tile_w=None):
+    """Host (pinned) inputs of one frame, its plan (on tiles tile_w pixels wide
+    if given) and its stand-alone image."""
     import torch
     beat = synth.workload_beat(wl)
     w_az = np.hanning(wl.n_pulses).astype(np.float32)
     plan = make_plan(wl, precision=precision)
+    if tile_w:
+        plan.set_tile_shape(tile_w)
     b, w, qt, qr = to_dev(wl, beat, w_az)
     alone = plan.backproject(plan.range_compress(b, w), wl.n_pulses, qt, qr)
     torch.cuda.synchronize()
@@ -49,7 +52,7 @@ def _frames(n, seed=21):
     out = []
     for i, wl in enumerate(synth.make_batched_requests(n, seed=seed, m_range=(60, 300),
                                                        side_range=(48, 224), n_samples=128)):
-        out.append(_frame(wl, precision=i % 2))
+        out.append(_frame(wl, precision=i % 2, tile_w=(None, 16, 64)[i % 3]))
     return out
 
 
@@ -93,8 +96,8 @@ def test_host_image_mapped_and_pageable_match_the_device_image():
 
 @pytest.mark.parametrize("chunk,quantum", [(48, 0), (4096, 2)], ids=["chunk48", "quantum2M"])
 def test_each_result_same_alone_and_in_the_mix(chunk, quantum):
-    """Twelve frames of different radars (plans, Rx counts, storages, sizes)
-    submitted together and while others run: every image equals the same
+    """Twelve frames of different radars (plans, Rx counts, storages, sizes,
+    tile shapes) submitted together and while others run: every image equals the same
     frame imaged alone, within the FP32 summation-order tolerance; with
     fixed chunks and with a work quantum per request and round."""
     import paper_2306_09784_gb300 as sar
